@@ -1,0 +1,147 @@
+/*
+ * dpg.h — C ABI of the GB300 (sm_103a) record-retrieval library.
+ *
+ * Record retrieval (Cooperman, Ma, Nguyen, "DPG: A Cache-Efficient Accelerator
+ * for Sorting and for Join Operators", §1 and §2): given a source table of
+ * fixed-size records, a sequence of record ids (rids) and a destination
+ * table, copy record rids[i] of the source into slot i of the destination:
+ *
+ *     for each i:  dst[i] = src[rids[i]]
+ *
+ * The library computes it with distribute-probe-gather (DPG, §2.1, Figure 1)
+ * as CUDA kernels, and offers the plain one-pass gather as a baseline, the
+ * copy phase of a key-pointer sort (§3) and the DPG-move / DPG-sort
+ * foreign-key joins (§4.2.1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Tables are packed arrays of records: record k of a table of `rec_bytes`
+ *    records starts at byte k * rec_bytes.  No padding, any alignment (wider
+ *    vector paths are taken when pointers and sizes allow).
+ *  - Pointers are DEVICE pointers owned by the caller unless a call says
+ *    otherwise.  The library never frees them and keeps no reference after
+ *    the call's GPU work has finished.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls are stream-ordered: they enqueue kernels and return.
+ *  - Argument errors (DPG_EINVAL) are detected on the host, before anything is
+ *    enqueued.  A rid (or foreign key) outside its table is detected on the
+ *    GPU before any destination byte is written: the destination is left
+ *    untouched and the NEXT dpg_sync on that context returns DPG_ERANGE.
+ *  - A context owns scratch memory, grown on demand with cudaMalloc; growth
+ *    synchronizes the device, so the first call at a given size should come
+ *    before any CUDA-graph capture.  One context serves one stream at a time:
+ *    calls on one context from several streams at once race on its scratch.
+ *  - Sizes: record counts and rid values fit in int32 (n, n_src <= 2^31 - 1).
+ */
+#ifndef DPG_H
+#define DPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DPG_OK = 0,
+  DPG_EINVAL = 1,    /* bad argument: null pointer, zero record size, overlap, size limit */
+  DPG_ERANGE = 2,    /* a rid / foreign key outside [0, n_src) (reported by dpg_sync) */
+  DPG_ENOMEM = 3,    /* scratch allocation failed */
+  DPG_ECUDA = 4,     /* a CUDA runtime call failed */
+  DPG_ETIMEOUT = 5,  /* a bounded device-side wait gave up (reported by dpg_sync) */
+  DPG_EBUSY = 6      /* resource held by another request (serving admission) */
+} dpg_status;
+
+typedef struct dpg_ctx dpg_ctx;
+
+/* Create a context on CUDA device `device` (it becomes current for the call).
+ * *out receives the handle. */
+dpg_status dpg_ctx_create(dpg_ctx** out, int device);
+
+/* Destroy a context: synchronizes its device and frees its scratch.  NULL is a no-op. */
+void dpg_ctx_destroy(dpg_ctx* ctx);
+
+/* A static, human-readable string for a status code. */
+const char* dpg_strerror(dpg_status status);
+
+/* Last CUDA error string recorded by the context (for DPG_ECUDA), or "". */
+const char* dpg_last_error(dpg_ctx* ctx);
+
+/*
+ * Record retrieval by distribute-probe-gather (§2.1, Figure 1).
+ *   src       n_src records of rec_bytes bytes (the INPUT file of §2.1)
+ *   rids      n int32 record ids, each in [0, n_src) (RID_LIST)
+ *   dst       n records of rec_bytes bytes (OUTPUT); must not overlap src
+ * Phase I partitions the rids by source segment (runs of 2^k records), Phase
+ * II loads each segment into shared memory and copies its records out in
+ * run order, Phase III writes the destination in rid order.  n == 0 is a no-op.
+ * Duplicated and skewed rids are allowed (§2, §2.3).
+ */
+dpg_status dpg_retrieve(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes,
+                        size_t n, const int32_t* rids, void* dst, void* stream);
+
+/* The same result by the plain one-pass gather (§1, "standard approach"):
+ * every destination record is read straight from its random source location.
+ * Baseline for comparison.  On a bad rid the destination is left partly
+ * written (slots with valid rids are copied) and dpg_sync returns DPG_ERANGE. */
+dpg_status dpg_retrieve_direct(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes,
+                               size_t n, const int32_t* rids, void* dst, void* stream);
+
+/*
+ * Copy phase of a three-phase key-pointer sort (§3, phase 3): `pairs` holds n
+ * sorted key-pointer pairs of pair_stride bytes whose int32 rid sits at byte
+ * rid_off (pair_stride and rid_off multiples of 4; the library's own pair
+ * layout is 16 bytes with the rid at byte 12).  dst[i] = src[rid of pairs[i]],
+ * by distribute-probe-gather.
+ */
+dpg_status dpg_sort_copy(dpg_ctx* ctx, const void* pairs, size_t pair_stride, size_t rid_off,
+                         size_t n, const void* src, size_t n_src, size_t rec_bytes, void* dst,
+                         void* stream);
+
+/* Plain one-pass gather for the sort copy phase (baseline). */
+dpg_status dpg_sort_copy_direct(dpg_ctx* ctx, const void* pairs, size_t pair_stride,
+                                size_t rid_off, size_t n, const void* src, size_t n_src,
+                                size_t rec_bytes, void* dst, void* stream);
+
+/* Blocks until `stream` has finished, then returns the first asynchronous
+ * error raised by this context's kernels since the previous dpg_sync
+ * (DPG_ERANGE, DPG_ETIMEOUT) and clears it; DPG_OK when there was none. */
+dpg_status dpg_sync(dpg_ctx* ctx, void* stream);
+
+/* Number of kernels this context has launched since it was created. */
+uint64_t dpg_kernel_launches(dpg_ctx* ctx);
+
+/*
+ * Host-buffer variants (the paper states retrieval between files, §1; here
+ * the "files" are host memory).  src/pairs, rids and dst are HOST pointers
+ * (page-locked memory gives full copy bandwidth).  The call copies the inputs
+ * into context-owned device buffers, runs the device entry point of the same
+ * name, copies the result back and synchronizes `stream`; it returns the final
+ * status, DPG_ERANGE included (dst untouched then).
+ */
+dpg_status dpg_retrieve_host(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes, size_t n,
+                             const int32_t* rids, void* dst, void* stream);
+dpg_status dpg_sort_copy_host(dpg_ctx* ctx, const void* pairs, size_t pair_stride, size_t rid_off,
+                              size_t n, const void* src, size_t n_src, size_t rec_bytes, void* dst,
+                              void* stream);
+
+/*
+ * Kernel tracing (measurement support; the paper has none).  While enabled,
+ * every kernel the context launches is bracketed by two CUDA events recorded
+ * on its stream.  dpg_trace_count / dpg_trace_get wait for the recorded
+ * events and report, per kernel name, the summed event time in milliseconds
+ * and the number of launches since the last dpg_trace_reset.  Names are owned
+ * by the context and stay valid until dpg_trace_reset or dpg_ctx_destroy.
+ */
+void dpg_trace_enable(dpg_ctx* ctx, int on);
+void dpg_trace_reset(dpg_ctx* ctx);
+size_t dpg_trace_count(dpg_ctx* ctx);
+dpg_status dpg_trace_get(dpg_ctx* ctx, size_t index, const char** name, double* total_ms,
+                         uint64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPG_H */

@@ -1,0 +1,119 @@
+// Device-side helpers shared by the record-retrieval kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dpg {
+
+// Bits of the context's device error word.
+enum : int { ERR_RANGE = 1, ERR_TIMEOUT = 2 };
+
+// Bounded device-side waits give up after this many SM clock cycles (~1 s).
+constexpr long long kWaitCycles = 2000000000LL;
+
+// q = n / d by a 64-bit multiply-high with m = ceil(2^64 / d).  Exact whenever
+// n * d < 2^64 (the error n * (m - 2^64/d) / 2^64 stays below 1/d); here
+// n < 2^48 and d < 2^17.  d == 1 is handled apart because m would be 2^64.
+struct FastDiv {
+  uint64_t m;
+  uint32_t d;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.m = (d <= 1) ? 0 : (UINT64_MAX / d + 1);
+  return f;
+}
+
+__device__ __forceinline__ uint64_t fdiv(uint64_t n, const FastDiv& f) {
+  return f.d == 1 ? n : __umul64hi(n, f.m);
+}
+
+// The unit in which a kernel moves record bytes: WB bytes, WB a power of two
+// that divides the record size and every base address involved.
+template <int WB> struct WordT;
+template <> struct WordT<16> { using T = uint4; };
+template <> struct WordT<8> { using T = uint2; };
+template <> struct WordT<4> { using T = uint32_t; };
+template <> struct WordT<2> { using T = uint16_t; };
+template <> struct WordT<1> { using T = uint8_t; };
+
+// Rid sources: a plain int32 array, or the int32 field of strided
+// key-pointer pairs.  Both address 4-byte-aligned int32 values.
+struct RidArray {
+  const int32_t* p;
+  __device__ __forceinline__ int32_t operator()(uint64_t i) const { return __ldg(p + i); }
+};
+struct RidStrided {
+  const uint8_t* base;  // points at the rid field of pair 0
+  uint32_t stride;
+  __device__ __forceinline__ int32_t operator()(uint64_t i) const {
+    return __ldg(reinterpret_cast<const int32_t*>(base + i * stride));
+  }
+};
+struct SlotArray {
+  const uint32_t* p;
+  __device__ __forceinline__ int32_t operator()(uint64_t i) const { return (int32_t)__ldg(p + i); }
+};
+
+__device__ __forceinline__ bool error_set(const int* err) {
+  return *reinterpret_cast<const volatile int*>(err) != 0;
+}
+
+// ---- mbarrier + bulk copy (inline PTX, sm_90 and later) --------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Global -> shared bulk copy completing on `bar`; dst, src 16-byte aligned,
+// bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar`, giving up after kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+}  // namespace dpg

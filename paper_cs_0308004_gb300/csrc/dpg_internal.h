@@ -1,0 +1,95 @@
+// Host-side internals of the record-retrieval library: the context object,
+// plans and the launch functions behind the C ABI in include/dpg.h.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dpg.h"
+
+struct dpg_ctx {
+  int device = 0;
+  int sms = 0;
+  size_t smem_optin = 0;     // max dynamic shared memory per block (opt-in)
+  int* d_err = nullptr;      // device error word (bits dpg::ERR_*)
+  int* h_err = nullptr;      // pinned host copy used by dpg_sync
+  void* scratch = nullptr;   // grown on demand
+  size_t scratch_bytes = 0;
+  uint64_t launches = 0;
+  std::string last_error;
+  // host-buffer entry points: device copies of the caller's tables
+  void* io = nullptr;
+  size_t io_bytes = 0;
+  // kernel tracing: CUDA events recorded around every launch on its stream
+  bool trace = false;
+  struct TraceRec {
+    const char* name;
+    cudaEvent_t start, stop;
+  };
+  std::vector<TraceRec> trace_pending;
+  std::vector<cudaEvent_t> trace_pool;
+  std::map<std::string, std::pair<double, uint64_t>> trace_totals;  // name -> (ms, launches)
+  std::vector<std::string> trace_names;                              // stable order for readers
+};
+
+namespace dpg {
+
+// How a retrieval is carried out.
+//   variant 3: Phase I distribute -> Phase II probe into an INTERNAL staging
+//              table in run order -> Phase III gather in rid order (Figure 1).
+//   variant 2: Phase I distribute -> Phase II probe writing each record
+//              straight to its destination slot (probe and gather fused).
+struct Plan {
+  int variant = 3;
+  int seg_log2 = 10;     // a source segment (run) holds 2^seg_log2 records
+  uint32_t chunk = 0;    // max rids per probe work item (0: 4 x segment)
+};
+
+// Where the rids come from: a plain int32 array, or the int32 field at a fixed
+// offset of strided key-pointer pairs.
+struct RidSpec {
+  const uint8_t* base;   // address of rid 0
+  uint32_t stride;       // bytes between consecutive rids (4 for a plain array)
+};
+
+struct Retrieval {
+  const uint8_t* src;
+  uint64_t n_src;
+  uint32_t rec;
+  uint64_t n;
+  RidSpec rids;
+  uint8_t* dst;
+  cudaStream_t stream;
+};
+
+// Limits of the DPG path.
+constexpr uint32_t kMaxDpgRecBytes = 65536;   // a segment holds at least one record
+constexpr uint32_t kSmemBuckets = 24576;      // Phase I per-CTA counters fit in 96 KB
+
+// Plan chosen for a retrieval (environment overrides DPG_VARIANT,
+// DPG_SEG_LOG2, DPG_CHUNK apply when set).
+Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r);
+
+// Enqueue the DPG retrieval / the direct gather.  Return a dpg_status.
+int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan);
+int run_direct(dpg_ctx& ctx, const Retrieval& r);
+
+// Scratch arena helpers (dpg_api.cu).
+int ensure_scratch(dpg_ctx& ctx, size_t bytes);
+int cuda_fail(dpg_ctx& ctx, cudaError_t e, const char* what);
+
+// Brackets one kernel launch with CUDA events on its stream when tracing is on.
+struct TraceScope {
+  dpg_ctx& ctx;
+  cudaStream_t stream;
+  bool on;
+  TraceScope(dpg_ctx& c, const char* name, cudaStream_t s);
+  ~TraceScope();
+};
+
+}  // namespace dpg

@@ -1,0 +1,605 @@
+// Record retrieval kernels for sm_103a: distribute-probe-gather (DPG, §2.1 and
+// Figure 1 of Cooperman, Ma, Nguyen) and the plain one-pass gather (§1).
+//
+// Notation: N = n_src source records of `rec` bytes, n rids, segments (the
+// paper's runs) of S = 2^seg_log2 consecutive source records, nb = ceil(N/S)
+// segments.  All arithmetic is integer.
+//
+//   K2 k_hist        Phase I, pass 1: per-CTA counts of rids per segment,
+//                    range check of every rid (before any destination write).
+//   K3 k_scan        Phase I: run offsets (exclusive scan of the counts),
+//                    per-(segment, CTA) write cursors and probe work items
+//                    (a segment with many rids is split into chunks, §2.3).
+//   K4 k_distribute  Phase I, pass 2: append each rid's in-segment offset to
+//                    its run (RID_RUN) and remember where it went.
+//   K5 k_probe       Phase II: bulk-copy one source segment into shared memory
+//                    (cp.async.bulk + mbarrier), then copy its records out in
+//                    run order, into the INTERNAL staging table (3-pass plan)
+//                    or straight into their destination slots (2-pass plan).
+//   K6 k_gather      Phase III: dst[i] = INTERNAL[slot[i]], written in rid
+//                    order as one coalesced stream.
+//   K1 k_gather      the baseline: dst[i] = src[rids[i]] in one pass.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+
+#include "dpg_device.cuh"
+#include "dpg_internal.h"
+
+namespace dpg {
+namespace {
+
+constexpr int kGatherThreads = 256;
+constexpr int kGatherUnroll = 8;
+constexpr int kPhaseThreads = 1024;
+constexpr int kProbeThreads = 512;
+constexpr uint32_t kSegBytesMax = 110 * 1024;  // two probe CTAs per SM
+constexpr uint32_t kBulkPiece = 32 * 1024;     // bytes per cp.async.bulk request
+constexpr int kDistUnroll = 4;
+
+// --------------------------------------------------------------- K1 / K6
+// dst[i] = src[idx(i)] for i in [0, n).  The destination is one contiguous
+// stream of WB-byte words; word t belongs to record i = t / W, word w = t % W,
+// and is read from word w of source record idx(i).  Each thread keeps
+// kGatherUnroll independent loads in flight.
+template <int WB, bool CHECK, class Idx>
+__global__ void __launch_bounds__(kGatherThreads)
+    k_gather(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, Idx idx, uint64_t n, uint32_t W,
+             FastDiv fdW, uint32_t n_src, int* err) {
+  using T = typename WordT<WB>::T;
+  if (!CHECK && error_set(err)) return;
+  const T* s = reinterpret_cast<const T*>(src);
+  T* d = reinterpret_cast<T*>(dst);
+  const uint64_t total = n * W;
+  const uint64_t step = (uint64_t)gridDim.x * kGatherThreads * kGatherUnroll;
+  bool bad = false;
+  for (uint64_t base = (uint64_t)blockIdx.x * kGatherThreads * kGatherUnroll + threadIdx.x; base < total;
+       base += step) {
+    T v[kGatherUnroll];
+    bool ok[kGatherUnroll];
+#pragma unroll
+    for (int k = 0; k < kGatherUnroll; ++k) {
+      const uint64_t t = base + (uint64_t)k * kGatherThreads;
+      ok[k] = false;
+      if (t < total) {
+        const uint64_t i = fdiv(t, fdW);
+        const uint32_t w = (uint32_t)(t - i * W);
+        const uint32_t r = (uint32_t)idx(i);
+        if (!CHECK || r < n_src) {
+          v[k] = s[(uint64_t)r * W + w];
+          ok[k] = true;
+        } else {
+          bad = true;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kGatherUnroll; ++k)
+      if (ok[k]) d[base + (uint64_t)k * kGatherThreads] = v[k];
+  }
+  if (CHECK && bad) atomicOr(err, ERR_RANGE);
+}
+
+// --------------------------------------------------------------------- K2
+// CTA g counts the rids of [g*per, (g+1)*per) per segment in shared memory and
+// writes its column of the bucket-major count matrix cnt[b*G + g]; tot[b]
+// accumulates the segment totals.  With more segments than shared counters
+// (smem_mode == 0) it counts straight into tot[] with global atomics.
+template <class Rid>
+__global__ void __launch_bounds__(kPhaseThreads)
+    k_hist(Rid rid, uint64_t n, uint32_t n_src, uint32_t seg_log2, uint32_t nb, uint32_t G, uint64_t per,
+           uint32_t* __restrict__ cnt, uint32_t* __restrict__ tot, int* err, int smem_mode) {
+  extern __shared__ uint32_t h[];
+  const uint32_t g = blockIdx.x;
+  if (smem_mode) {
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+  }
+  const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
+  bool bad = false;
+  for (uint64_t i0 = lo + threadIdx.x; i0 < hi; i0 += (uint64_t)kDistUnroll * blockDim.x) {
+    int32_t r[kDistUnroll];
+#pragma unroll
+    for (int k = 0; k < kDistUnroll; ++k) {
+      const uint64_t i = i0 + (uint64_t)k * blockDim.x;
+      r[k] = i < hi ? rid(i) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kDistUnroll; ++k) {
+      const uint64_t i = i0 + (uint64_t)k * blockDim.x;
+      if (i < hi) {
+        if ((uint32_t)r[k] >= n_src) {
+          bad = true;
+        } else {
+          const uint32_t b = (uint32_t)r[k] >> seg_log2;
+          if (smem_mode) atomicAdd(&h[b], 1u);
+          else atomicAdd(&tot[b], 1u);
+        }
+      }
+    }
+  }
+  if (bad) atomicOr(err, ERR_RANGE);
+  if (smem_mode) {
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+      const uint32_t c = h[b];
+      cnt[(uint64_t)b * G + g] = c;
+      if (c) atomicAdd(&tot[b], c);
+    }
+  }
+}
+
+// --------------------------------------------------------------------- K3
+constexpr uint32_t kScanTile = 1024;  // segments per tile of the two-level scan
+
+// K3a: per tile of kScanTile segments, the sum of the rid counts and of the
+// probe work items (ceil(count / chunk)).
+__global__ void __launch_bounds__(1024)
+    k_tile_sums(const uint32_t* __restrict__ tot, uint32_t nb, uint32_t chunk, uint32_t* __restrict__ tsum,
+                uint32_t* __restrict__ isum, const int* err) {
+  __shared__ uint32_t s_t[32], s_i[32];
+  if (error_set(err)) return;
+  const uint32_t b = blockIdx.x * kScanTile + threadIdx.x;
+  uint32_t t = b < nb ? tot[b] : 0, it = (t + chunk - 1) / chunk;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+    it += __shfl_xor_sync(0xffffffffu, it, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_t[warp] = t;
+    s_i[warp] = it;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    t = s_t[lane];
+    it = s_i[lane];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      t += __shfl_xor_sync(0xffffffffu, t, o);
+      it += __shfl_xor_sync(0xffffffffu, it, o);
+    }
+    if (lane == 0) {
+      tsum[blockIdx.x] = t;
+      isum[blockIdx.x] = it;
+    }
+  }
+}
+
+// K3b: block x owns segments [32x, 32x+32).  It adds the tile sums of earlier
+// tiles and the counts of earlier segments of its own tile, scans its 32
+// segments (off[], itemoff[]), then each warp turns one row of the count
+// matrix into write cursors: cnt[b*G + g] <- off[b] + sum_{g' < g} cnt[b*G + g'].
+__global__ void __launch_bounds__(1024)
+    k_scan(const uint32_t* __restrict__ tot, const uint32_t* __restrict__ tsum, const uint32_t* __restrict__ isum,
+           uint32_t nb, uint32_t G, uint32_t chunk, uint32_t* __restrict__ cnt, uint32_t* __restrict__ off,
+           uint32_t* __restrict__ itemoff, uint32_t* item_counter, const int* err) {
+  __shared__ uint32_t s_t[32], s_i[32], s_off[32];
+  if (error_set(err)) return;
+  const uint32_t b0 = blockIdx.x * 32;
+  const uint32_t tile = b0 / kScanTile, tile_start = tile * kScanTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t st = 0, si = 0;
+  for (uint32_t x = threadIdx.x; x < tile; x += blockDim.x) {
+    st += tsum[x];
+    si += isum[x];
+  }
+  for (uint32_t b = tile_start + threadIdx.x; b < b0; b += blockDim.x) {
+    const uint32_t t = tot[b];
+    st += t;
+    si += (t + chunk - 1) / chunk;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    st += __shfl_xor_sync(0xffffffffu, st, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) {
+    s_t[warp] = st;
+    s_i[warp] = si;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t a = s_t[lane], c = s_i[lane];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const uint32_t b = b0 + lane;
+    const uint32_t t = b < nb ? tot[b] : 0;
+    const uint32_t it = (t + chunk - 1) / chunk;
+    uint32_t ti = t, ii = it;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, ti, o), y = __shfl_up_sync(0xffffffffu, ii, o);
+      if (lane >= o) {
+        ti += x;
+        ii += y;
+      }
+    }
+    const uint32_t eo = a + ti - t, ei = c + ii - it;
+    s_off[lane] = eo;
+    if (b < nb) {
+      off[b] = eo;
+      itemoff[b] = ei;
+    }
+    if (b + 1 == nb) {
+      off[nb] = a + ti;
+      itemoff[nb] = c + ii;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *item_counter = 0;
+  __syncthreads();
+  const uint32_t b = b0 + warp;
+  if (b < nb) {
+    uint32_t run = s_off[warp];
+    uint32_t* row = cnt + (uint64_t)b * G;
+    for (uint32_t c0 = 0; c0 < G; c0 += 32) {
+      const uint32_t c = c0 + lane;
+      const uint32_t v = c < G ? row[c] : 0;
+      uint32_t incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+      }
+      if (c < G) row[c] = run + incl - v;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
+// --------------------------------------------------------------------- K4
+// CTA g re-reads the rids of [g*per, (g+1)*per) and appends each one's offset
+// inside its segment to that segment's run at the CTA's cursor.  SLOT: the
+// 3-pass plan records slot[i] = run position of rid i; otherwise the 2-pass
+// plan records dest[pos] = i.  Rids are taken in sub-tiles separated by a
+// barrier, so within a run the entries of one CTA keep rid order up to
+// reordering inside a sub-tile of kDistUnroll * blockDim rids.
+template <class Rid, typename LoT, bool SLOT>
+__global__ void __launch_bounds__(kPhaseThreads)
+    k_distribute(Rid rid, uint64_t n, uint32_t seg_log2, uint32_t nb, uint32_t G, uint64_t per,
+                 uint32_t* __restrict__ cur_g, LoT* __restrict__ lo_out, uint32_t* __restrict__ side,
+                 const int* err, int smem_mode) {
+  extern __shared__ uint32_t cur[];
+  if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
+  const uint32_t g = blockIdx.x;
+  if (smem_mode) {
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cur[b] = cur_g[(uint64_t)b * G + g];
+    __syncthreads();
+  }
+  const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
+  const uint32_t mask = (1u << seg_log2) - 1u;
+  const uint64_t tile = (uint64_t)kDistUnroll * blockDim.x;
+  int32_t r[kDistUnroll];
+#pragma unroll
+  for (int k = 0; k < kDistUnroll; ++k) {
+    const uint64_t i = lo + (uint64_t)k * blockDim.x + threadIdx.x;
+    r[k] = i < hi ? rid(i) : 0;
+  }
+  for (uint64_t t0 = lo; t0 < hi; t0 += tile) {
+    int32_t nr[kDistUnroll];
+#pragma unroll
+    for (int k = 0; k < kDistUnroll; ++k) {
+      const uint64_t i = t0 + tile + (uint64_t)k * blockDim.x + threadIdx.x;
+      nr[k] = i < hi ? rid(i) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kDistUnroll; ++k) {
+      const uint64_t i = t0 + (uint64_t)k * blockDim.x + threadIdx.x;
+      if (i < hi) {
+        const uint32_t rv = (uint32_t)r[k];
+        const uint32_t b = rv >> seg_log2;
+        const uint32_t pos = smem_mode ? atomicAdd(&cur[b], 1u) : atomicAdd(&cur_g[b], 1u);
+        lo_out[pos] = (LoT)(rv & mask);
+        if (SLOT) side[i] = pos;
+        else side[pos] = (uint32_t)i;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kDistUnroll; ++k) r[k] = nr[k];
+  }
+}
+
+// ------------------------------------------------------------------ K5/K7
+// Persistent CTAs take work items (segment b, chunk c) from a global counter.
+// A new segment is copied into shared memory with cp.async.bulk (16-byte
+// aligned source) or with plain vector loads; then the chunk's run entries
+// [p0, p1) are served from shared memory: word w of entry k is copied to
+// out[k] (INTERNAL staging, 3-pass) or to out[dest[k]] (the destination, 2-pass).
+template <int WB, typename LoT, bool SCATTER>
+__global__ void __launch_bounds__(kProbeThreads)
+    k_probe(const uint8_t* __restrict__ src, uint32_t n_src, uint32_t rec, uint32_t seg_log2,
+            const uint32_t* __restrict__ off, const uint32_t* __restrict__ itemoff, uint32_t nb, uint32_t chunk,
+            const LoT* __restrict__ lo, const uint32_t* __restrict__ dest, uint8_t* __restrict__ out, uint32_t W,
+            FastDiv fdW, int* err, uint32_t* item_counter, int use_bulk) {
+  using T = typename WordT<WB>::T;
+  extern __shared__ __align__(128) uint8_t seg[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t s_item, s_b;
+  if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const uint32_t n_items = itemoff[nb];
+  uint32_t phase = 0;
+  int64_t loaded = -1;
+  const T* sw = reinterpret_cast<const T*>(seg);
+  T* ow = reinterpret_cast<T*>(out);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t it = atomicAdd(item_counter, 1u);
+      s_item = it;
+      if (it < n_items) {
+        uint32_t a = 0, z = nb;  // first j with itemoff[j] > it; itemoff[0] = 0 <= it
+        while (a < z) {
+          const uint32_t m = (a + z) >> 1;
+          if (itemoff[m] > it) z = m;
+          else a = m + 1;
+        }
+        s_b = a - 1;
+      }
+    }
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= n_items) break;
+    const uint32_t b = s_b;
+    if ((int64_t)b != loaded) {
+      const uint64_t first = (uint64_t)b << seg_log2;
+      const uint64_t left = (uint64_t)n_src - first;
+      const uint32_t nrec = (uint32_t)(left < (1ull << seg_log2) ? left : (1ull << seg_log2));
+      const uint32_t bytes = nrec * rec;
+      const uint8_t* gsrc = src + first * rec;
+      if (use_bulk) {
+        const uint32_t body = bytes & ~15u;
+        if (threadIdx.x == 0 && body) {
+          fence_proxy_async_smem();
+          mbar_arrive_expect_tx(&bar, body);
+          for (uint32_t o = 0; o < body; o += kBulkPiece) bulk_g2s(seg + o, gsrc + o, min(kBulkPiece, body - o), &bar);
+        }
+        for (uint32_t o = body + threadIdx.x; o < bytes; o += blockDim.x) seg[o] = gsrc[o];
+        if (body) {
+          const bool ok = mbar_wait_bounded(&bar, phase);
+          if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+              atomicOr(err, ERR_TIMEOUT);
+              mbar_wait_bounded(&bar, phase);  // let the copy in flight land before exiting
+            }
+            return;
+          }
+          phase ^= 1u;
+        }
+      } else {
+        const T* gw = reinterpret_cast<const T*>(gsrc);
+        T* sd = reinterpret_cast<T*>(seg);
+        for (uint32_t o = threadIdx.x; o < bytes / WB; o += blockDim.x) sd[o] = gw[o];
+      }
+      __syncthreads();
+      loaded = b;
+    }
+    const uint32_t p0 = off[b] + (item - itemoff[b]) * chunk;
+    const uint32_t p1 = min(off[b + 1], p0 + chunk);
+    const uint64_t total = (uint64_t)(p1 - p0) * W;
+    for (uint64_t t = threadIdx.x; t < total; t += blockDim.x) {
+      const uint64_t q = fdiv(t, fdW);
+      const uint32_t w = (uint32_t)(t - q * W);
+      const uint64_t k = p0 + q;
+      const T v = sw[(uint64_t)lo[k] * W + w];
+      if (SCATTER) ow[(uint64_t)dest[k] * W + w] = v;
+      else ow[k * W + w] = v;
+    }
+    fence_proxy_async_smem();  // order this CTA's shared-memory accesses before the next bulk copy
+    __syncthreads();
+  }
+}
+
+// Sets the range bit when n > 0 rids address an empty source table.
+__global__ void k_flag_range(int* err) { atomicOr(err, ERR_RANGE); }
+
+// ------------------------------------------------------------------ host side
+
+inline uint32_t pow2_align(uint64_t x) {
+  uint32_t w = 16;
+  while (w > 1 && (x % w)) w >>= 1;
+  return w;
+}
+
+template <class K>
+void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return (v && *v) ? std::atoi(v) : dflt;
+}
+
+template <class Idx, bool CHECK>
+void launch_gather(dpg_ctx& ctx, uint32_t WB, const uint8_t* src, uint8_t* dst, Idx idx, uint64_t n, uint32_t rec,
+                   uint32_t n_src, cudaStream_t st) {
+  const uint32_t W = rec / WB;
+  const FastDiv f = make_fastdiv(W);
+  const uint64_t total = n * W;
+  const uint64_t per_block = (uint64_t)kGatherThreads * kGatherUnroll;
+  const uint64_t want = (total + per_block - 1) / per_block;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx.sms * 8));
+  TraceScope ts(ctx, CHECK ? "k_gather_direct" : "k_gather_phase3", st);
+  switch (WB) {
+    case 16: k_gather<16, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
+    case 8: k_gather<8, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
+    case 4: k_gather<4, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
+    case 2: k_gather<2, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
+    default: k_gather<1, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
+  }
+  ctx.launches++;
+}
+
+template <typename LoT, bool SCATTER>
+void launch_probe(dpg_ctx& ctx, uint32_t WB, const Retrieval& r, uint32_t seg_log2, const uint32_t* off,
+                  const uint32_t* itemoff, uint32_t nb, uint32_t chunk, const LoT* lo, const uint32_t* dest,
+                  uint8_t* out, uint32_t* counter, int use_bulk, size_t smem) {
+  const uint32_t W = r.rec / WB;
+  const FastDiv f = make_fastdiv(W);
+  const int grid = ctx.sms * 2;
+  TraceScope ts(ctx, SCATTER ? "k_probe_scatter" : "k_probe", r.stream);
+#define DPG_PROBE(WBV)                                                                                         \
+  {                                                                                                            \
+    auto kern = k_probe<WBV, LoT, SCATTER>;                                                                    \
+    set_smem(kern, smem);                                                                                      \
+    kern<<<grid, kProbeThreads, smem, r.stream>>>(r.src, (uint32_t)r.n_src, r.rec, seg_log2, off, itemoff, nb, \
+                                                 chunk, lo, dest, out, W, f, ctx.d_err, counter, use_bulk);    \
+  }
+  switch (WB) {
+    case 16: DPG_PROBE(16) break;
+    case 8: DPG_PROBE(8) break;
+    case 4: DPG_PROBE(4) break;
+    case 2: DPG_PROBE(2) break;
+    default: DPG_PROBE(1) break;
+  }
+#undef DPG_PROBE
+  ctx.launches++;
+}
+
+template <class Rid, typename LoT>
+int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
+  const uint32_t sl = (uint32_t)plan.seg_log2;
+  const uint64_t S = 1ull << sl;
+  const uint32_t nb = (uint32_t)((r.n_src + S - 1) >> sl);
+  const bool smem_mode = nb <= kSmemBuckets;
+  const uint32_t grid = (uint32_t)std::max<uint64_t>(
+      1, std::min<uint64_t>((uint64_t)ctx.sms * 2, (r.n + 8191) / 8192));
+  const uint32_t G = smem_mode ? grid : 1;
+  const uint64_t per = (r.n + grid - 1) / grid;
+  const uint32_t chunk = plan.chunk ? plan.chunk : (uint32_t)std::min<uint64_t>(4 * S, 1u << 20);
+  const bool three = plan.variant != 2;
+
+  // scratch layout, each piece 256-byte aligned
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_cnt = al((size_t)nb * G * 4), b_tot = al((size_t)nb * 4), b_off = al(((size_t)nb + 1) * 4);
+  const size_t b_ctr = 256, b_lo = al(r.n * sizeof(LoT)), b_side = al(r.n * 4);
+  const size_t b_ts = al((size_t)((nb + kScanTile - 1) / kScanTile) * 4);
+  const size_t b_stage = three ? al(r.n * r.rec) : 0;
+  const size_t need = b_cnt + b_tot + 2 * b_off + b_ctr + 2 * b_ts + b_lo + b_side + b_stage;
+  if (int s = ensure_scratch(ctx, need)) return s;
+  uint8_t* p = static_cast<uint8_t*>(ctx.scratch);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(p); p += b_cnt;
+  uint32_t* tot = reinterpret_cast<uint32_t*>(p); p += b_tot;
+  uint32_t* off = reinterpret_cast<uint32_t*>(p); p += b_off;
+  uint32_t* itemoff = reinterpret_cast<uint32_t*>(p); p += b_off;
+  uint32_t* counter = reinterpret_cast<uint32_t*>(p); p += b_ctr;
+  uint32_t* tsum = reinterpret_cast<uint32_t*>(p); p += b_ts;
+  uint32_t* isum = reinterpret_cast<uint32_t*>(p); p += b_ts;
+  LoT* lo = reinterpret_cast<LoT*>(p); p += b_lo;
+  uint32_t* side = reinterpret_cast<uint32_t*>(p); p += b_side;
+  uint8_t* stage = three ? p : nullptr;
+
+  cudaError_t e = cudaMemsetAsync(tot, 0, (size_t)nb * 4, r.stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  const size_t phase_smem = smem_mode ? (size_t)nb * 4 : 0;
+  {
+    TraceScope ts(ctx, "k_hist", r.stream);
+    auto kern = k_hist<Rid>;
+    set_smem(kern, phase_smem);
+    kern<<<grid, kPhaseThreads, phase_smem, r.stream>>>(rid, r.n, (uint32_t)r.n_src, sl, nb, G, per, cnt, tot,
+                                                        ctx.d_err, smem_mode);
+    ctx.launches++;
+  }
+  const uint32_t ntiles = (nb + kScanTile - 1) / kScanTile;
+  {
+    TraceScope ts(ctx, "k_tile_sums", r.stream);
+    k_tile_sums<<<ntiles, kScanTile, 0, r.stream>>>(tot, nb, chunk, tsum, isum, ctx.d_err);
+  }
+  {
+    TraceScope ts(ctx, "k_scan", r.stream);
+    k_scan<<<(nb + 31) / 32, 1024, 0, r.stream>>>(tot, tsum, isum, nb, G, chunk, cnt, off, itemoff, counter,
+                                                  ctx.d_err);
+  }
+  ctx.launches += 2;
+  {
+    TraceScope ts(ctx, "k_distribute", r.stream);
+    auto kern = three ? k_distribute<Rid, LoT, true> : k_distribute<Rid, LoT, false>;
+    set_smem(kern, phase_smem);
+    kern<<<grid, kPhaseThreads, phase_smem, r.stream>>>(rid, r.n, sl, nb, G, per, cnt, lo, side, ctx.d_err,
+                                                        smem_mode);
+    ctx.launches++;
+  }
+  // Phase II: word size limited by the record size, the shared-memory record
+  // offsets, and the output base (staging is 256-byte aligned).
+  const uintptr_t src_a = reinterpret_cast<uintptr_t>(r.src);
+  const uint32_t seg_bytes = (uint32_t)(std::min<uint64_t>(S, r.n_src) * r.rec);
+  const int use_bulk = (src_a % 16 == 0) && ((S * r.rec) % 16 == 0);
+  uint32_t wb_probe = pow2_align(r.rec);
+  if (!three) wb_probe = std::min(wb_probe, pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
+  if (!use_bulk) wb_probe = std::min(wb_probe, pow2_align(src_a));
+  const size_t probe_smem = ((size_t)seg_bytes + 15) & ~size_t(15);
+  if (three)
+    launch_probe<LoT, false>(ctx, wb_probe, r, sl, off, itemoff, nb, chunk, lo, nullptr, stage, counter, use_bulk,
+                             probe_smem);
+  else
+    launch_probe<LoT, true>(ctx, wb_probe, r, sl, off, itemoff, nb, chunk, lo, side, r.dst, counter, use_bulk,
+                            probe_smem);
+  if (three) {
+    // Phase III
+    const uint32_t wb = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
+    launch_gather<SlotArray, false>(ctx, wb, stage, r.dst, SlotArray{side}, r.n, r.rec, (uint32_t)r.n_src,
+                                    r.stream);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "dpg launch");
+  return DPG_OK;
+}
+
+}  // namespace
+
+Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
+  (void)ctx;
+  Plan p;
+  int sl = 0;
+  while (sl < 30 && ((2ull << sl) * r.rec) <= kSegBytesMax) ++sl;
+  // keep the number of segments within the shared-memory counters if possible
+  p.seg_log2 = sl;
+  p.variant = env_int("DPG_VARIANT", 3);
+  const int o = env_int("DPG_SEG_LOG2", -1);
+  if (o >= 0 && (1ull << o) * r.rec <= kSegBytesMax) p.seg_log2 = o;
+  p.chunk = (uint32_t)env_int("DPG_CHUNK", 0);
+  return p;
+}
+
+int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {
+  if (r.n == 0) return DPG_OK;
+  if (r.n_src == 0) {
+    k_flag_range<<<1, 1, 0, r.stream>>>(ctx.d_err);
+    ctx.launches++;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "flag");
+  }
+  if ((1ull << plan.seg_log2) * r.rec > kSegBytesMax && plan.seg_log2 > 0) return DPG_EINVAL;
+  const bool lo16 = plan.seg_log2 <= 16;
+  if (r.rids.stride == 4) {
+    RidArray a{reinterpret_cast<const int32_t*>(r.rids.base)};
+    return lo16 ? run_dpg_t<RidArray, uint16_t>(ctx, r, a, plan) : run_dpg_t<RidArray, uint32_t>(ctx, r, a, plan);
+  }
+  RidStrided s{r.rids.base, r.rids.stride};
+  return lo16 ? run_dpg_t<RidStrided, uint16_t>(ctx, r, s, plan) : run_dpg_t<RidStrided, uint32_t>(ctx, r, s, plan);
+}
+
+int run_direct(dpg_ctx& ctx, const Retrieval& r) {
+  if (r.n == 0) return DPG_OK;
+  const uint32_t wb = std::min({pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.src)),
+                                pow2_align(reinterpret_cast<uintptr_t>(r.dst))});
+  if (r.rids.stride == 4)
+    launch_gather<RidArray, true>(ctx, wb, r.src, r.dst, RidArray{reinterpret_cast<const int32_t*>(r.rids.base)},
+                                  r.n, r.rec, (uint32_t)r.n_src, r.stream);
+  else
+    launch_gather<RidStrided, true>(ctx, wb, r.src, r.dst, RidStrided{r.rids.base, r.rids.stride}, r.n, r.rec,
+                                    (uint32_t)r.n_src, r.stream);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "direct launch");
+}
+
+}  // namespace dpg

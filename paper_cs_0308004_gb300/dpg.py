@@ -1,0 +1,235 @@
+"""Python binding of the C ABI in include/dpg.h (argument marshalling only).
+
+Every computation runs in the CUDA kernels of libdpg.so; PyTorch supplies
+device memory and the current stream.  If the library has not been built the
+import fails: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdpg.so")
+
+# status codes (dpg_status)
+OK, EINVAL, ERANGE, ENOMEM, ECUDA, ETIMEOUT, EBUSY = range(7)
+
+# key-pointer pair layout used by the sort path: key bytes, zero padding,
+# int32 rid at byte 12; 16 bytes per pair
+PAIR_BYTES = 16
+PAIR_RID_OFF = 12
+
+# every symbol include/dpg.h declares, with its ctypes signature
+_P, _S, _U64, _I = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int
+SIGNATURES = {
+    "dpg_ctx_create": ([ctypes.POINTER(ctypes.c_void_p), _I], _I),
+    "dpg_ctx_destroy": ([_P], None),
+    "dpg_strerror": ([_I], ctypes.c_char_p),
+    "dpg_last_error": ([_P], ctypes.c_char_p),
+    "dpg_retrieve": ([_P, _P, _S, _S, _S, _P, _P, _P], _I),
+    "dpg_retrieve_direct": ([_P, _P, _S, _S, _S, _P, _P, _P], _I),
+    "dpg_sort_copy": ([_P, _P, _S, _S, _S, _P, _S, _S, _P, _P], _I),
+    "dpg_sort_copy_direct": ([_P, _P, _S, _S, _S, _P, _S, _S, _P, _P], _I),
+    "dpg_sync": ([_P, _P], _I),
+    "dpg_kernel_launches": ([_P], _U64),
+    "dpg_retrieve_host": ([_P, _P, _S, _S, _S, _P, _P, _P], _I),
+    "dpg_sort_copy_host": ([_P, _P, _S, _S, _S, _P, _S, _S, _P, _P], _I),
+    "dpg_trace_enable": ([_P, _I], None),
+    "dpg_trace_reset": ([_P], None),
+    "dpg_trace_count": ([_P], _S),
+    "dpg_trace_get": ([_P, _S, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_uint64)], _I),
+}
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"`"
+                          " (the CUDA library has no fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (args, res) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+class DpgError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        msg = f"{what}: {lib.dpg_strerror(status).decode()}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class DpgRangeError(DpgError, IndexError):
+    pass
+
+
+def _stream_handle(stream, device) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _need_cuda(t: torch.Tensor, name: str, device: torch.device):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library works on device memory only)")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the context on {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _table(t: torch.Tensor, name: str) -> tuple[int, int]:
+    if t.dtype != torch.uint8 or t.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D uint8 tensor (records x bytes)")
+    return t.shape[0], t.shape[1]
+
+
+class Context:
+    """Owns a dpg_ctx (scratch memory and the asynchronous error word)."""
+
+    def __init__(self, device: int | torch.device | None = None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", device if isinstance(device, int) else device.index)
+        h = ctypes.c_void_p()
+        self._check(lib.dpg_ctx_create(ctypes.byref(h), self.device.index), "dpg_ctx_create", h=None)
+        self._h = h
+
+    # -- plumbing
+    def _check(self, status: int, what: str, h=0):
+        if status != OK:
+            handle = self._h if h == 0 else h
+            detail = lib.dpg_last_error(handle).decode() if handle else ""
+            cls = DpgRangeError if status == ERANGE else DpgError
+            raise cls(status, what, detail)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.dpg_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(lib.dpg_kernel_launches(self._h))
+
+    # -- operations
+    def _retrieve(self, fn, src, rids, out, stream):
+        _need_cuda(src, "src", self.device)
+        _need_cuda(rids, "rids", self.device)
+        if rids.dtype != torch.int32 or rids.dim() != 1:
+            raise ValueError("rids must be a 1-D int32 tensor")
+        n_src, rec = _table(src, "src")
+        n = rids.shape[0]
+        if out is None:
+            out = torch.empty((n, rec), dtype=torch.uint8, device=self.device)
+        _need_cuda(out, "out", self.device)
+        if tuple(out.shape) != (n, rec) or out.dtype != torch.uint8:
+            raise ValueError("out must be a uint8 tensor of shape (len(rids), record bytes)")
+        st = fn(self._h, src.data_ptr(), n_src, rec, n, rids.data_ptr(), out.data_ptr(),
+                _stream_handle(stream, self.device))
+        self._check(st, fn.__name__)
+        return out
+
+    def retrieve(self, src: torch.Tensor, rids: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """dst[i] = src[rids[i]] by distribute-probe-gather (asynchronous; call sync())."""
+        return self._retrieve(lib.dpg_retrieve, src, rids, out, stream)
+
+    def retrieve_direct(self, src: torch.Tensor, rids: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """The same result by the plain one-pass gather (baseline)."""
+        return self._retrieve(lib.dpg_retrieve_direct, src, rids, out, stream)
+
+    def _sort_copy(self, fn, pairs, src, rid_off, out, stream):
+        _need_cuda(pairs, "pairs", self.device)
+        _need_cuda(src, "src", self.device)
+        n, stride = _table(pairs, "pairs")
+        n_src, rec = _table(src, "src")
+        if out is None:
+            out = torch.empty((n, rec), dtype=torch.uint8, device=self.device)
+        _need_cuda(out, "out", self.device)
+        if tuple(out.shape) != (n, rec) or out.dtype != torch.uint8:
+            raise ValueError("out must be a uint8 tensor of shape (pairs, record bytes)")
+        st = fn(self._h, pairs.data_ptr(), stride, rid_off, n, src.data_ptr(), n_src, rec, out.data_ptr(),
+                _stream_handle(stream, self.device))
+        self._check(st, fn.__name__)
+        return out
+
+    def sort_copy(self, pairs, src, rid_off: int = PAIR_RID_OFF, out=None, stream=None):
+        """Copy phase of a key-pointer sort (§3): dst[i] = src[rid of pairs[i]]."""
+        return self._sort_copy(lib.dpg_sort_copy, pairs, src, rid_off, out, stream)
+
+    def sort_copy_direct(self, pairs, src, rid_off: int = PAIR_RID_OFF, out=None, stream=None):
+        return self._sort_copy(lib.dpg_sort_copy_direct, pairs, src, rid_off, out, stream)
+
+    # -- host buffers (copies in and out happen inside the library)
+    @staticmethod
+    def _host(t, name):
+        if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor (pinned for full copy speed)")
+
+    def retrieve_host(self, src: torch.Tensor, rids: torch.Tensor, out: torch.Tensor, stream=None):
+        """Host-memory retrieval: copy in, DPG on the device, copy out; synchronous."""
+        for t, nm in ((src, "src"), (rids, "rids"), (out, "out")):
+            self._host(t, nm)
+        n_src, rec = _table(src, "src")
+        st = lib.dpg_retrieve_host(self._h, src.data_ptr(), n_src, rec, rids.shape[0], rids.data_ptr(),
+                                   out.data_ptr(), _stream_handle(stream, self.device))
+        self._check(st, "dpg_retrieve_host")
+        return out
+
+    def sort_copy_host(self, pairs: torch.Tensor, src: torch.Tensor, out: torch.Tensor,
+                       rid_off: int = PAIR_RID_OFF, stream=None):
+        for t, nm in ((pairs, "pairs"), (src, "src"), (out, "out")):
+            self._host(t, nm)
+        n, stride = _table(pairs, "pairs")
+        n_src, rec = _table(src, "src")
+        st = lib.dpg_sort_copy_host(self._h, pairs.data_ptr(), stride, rid_off, n, src.data_ptr(), n_src, rec,
+                                    out.data_ptr(), _stream_handle(stream, self.device))
+        self._check(st, "dpg_sort_copy_host")
+        return out
+
+    # -- kernel tracing (CUDA events around every launch)
+    def trace(self, on: bool = True):
+        lib.dpg_trace_enable(self._h, 1 if on else 0)
+
+    def trace_reset(self):
+        lib.dpg_trace_reset(self._h)
+
+    def trace_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last trace_reset."""
+        out = {}
+        for i in range(lib.dpg_trace_count(self._h)):
+            name, ms, cnt = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_uint64()
+            self._check(lib.dpg_trace_get(self._h, i, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(cnt)),
+                        "dpg_trace_get")
+            out[name.value.decode()] = (ms.value, cnt.value)
+        return out
+
+    def sync(self, stream=None):
+        """Wait for the stream; raise the first asynchronous error (bad rid, timeout)."""
+        self._check(lib.dpg_sync(self._h, _stream_handle(stream, self.device)), "dpg_sync")

@@ -1,0 +1,231 @@
+"""Parity of the CUDA retrieval path with the oracle, byte for byte.
+
+Every case compares dpg_retrieve (distribute-probe-gather, both the 3-pass and
+the 2-pass plan) and dpg_retrieve_direct with oracle.retrieve on the same
+seeded inputs: permutations, duplicates and skew (§2, §2.3), record sizes from
+1 to 4096 bytes, ragged tails, unaligned tables, forced small segments (the
+global-counter path and chunk splitting), empty and degenerate inputs, bad
+rids, and the full-size workloads on sampled outputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_cs_0308004_gb300 import dpg
+    c = dpg.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def rid_sequence(kind, n_src, n, seed):
+    if kind == "perm":
+        return synth.permutation(n_src, seed)[:n] if n <= n_src else synth.uniform_ids(n, n_src, seed)
+    if kind == "dup":
+        return synth.uniform_ids(n, n_src, seed)
+    if kind == "skew":
+        return synth.take(synth.zipf_ranks(n, n_src, 1.1, seed), synth.permutation(n_src, seed + 1))
+    if kind == "same":
+        return np.full(n, n_src // 2, dtype=np.int32)
+    raise ValueError(kind)
+
+
+def check(ctx, src, rids, variants=("dpg", "direct")):
+    want = oracle.retrieve(src, rids)
+    d_src, d_rids = to_dev(src), to_dev(rids)
+    for v in variants:
+        out = torch.full((rids.size, src.shape[1]), 0xA5, dtype=torch.uint8, device=DEV)
+        fn = ctx.retrieve if v == "dpg" else ctx.retrieve_direct
+        fn(d_src, d_rids, out=out)
+        ctx.sync()
+        got = out.cpu().numpy()
+        if not np.array_equal(got, want):
+            bad = np.nonzero(np.any(got != want, axis=1))[0]
+            raise AssertionError(f"{v}: {bad.size} records differ, first at {bad[:5]}")
+
+
+RECS = [1, 2, 3, 4, 7, 8, 12, 16, 17, 32, 64, 100, 128, 255, 256, 1000, 4096]
+
+
+@pytest.mark.parametrize("variant", ["3", "2"])
+@pytest.mark.parametrize("kind", ["perm", "dup", "skew"])
+@pytest.mark.parametrize("rec", RECS)
+def test_retrieve_matches_oracle(ctx, monkeypatch, rec, kind, variant):
+    monkeypatch.setenv("DPG_VARIANT", variant)
+    n_src = max(37, min(60000, (3 << 20) // rec)) | 1       # several segments and a ragged tail
+    n = n_src + 333 if kind != "perm" else n_src
+    src = synth.records(n_src, rec, rec)
+    check(ctx, src, rid_sequence(kind, n_src, n, 7 + rec))
+
+
+@pytest.mark.parametrize("variant", ["3", "2"])
+@pytest.mark.parametrize("seg_log2,chunk", [(0, 0), (1, 3), (3, 5), (5, 1000), (7, 64)])
+def test_forced_small_segments(ctx, monkeypatch, seg_log2, chunk, variant):
+    """Tiny segments give more segments than shared-memory counters (global
+    counter path); small chunks split every run into many probe items."""
+    monkeypatch.setenv("DPG_VARIANT", variant)
+    monkeypatch.setenv("DPG_SEG_LOG2", str(seg_log2))
+    monkeypatch.setenv("DPG_CHUNK", str(chunk))
+    n_src, rec = 50001, 12
+    src = synth.records(n_src, rec, 3)
+    for kind in ("perm", "dup", "same"):
+        check(ctx, src, rid_sequence(kind, n_src, 70001 if kind != "perm" else n_src, 9), variants=("dpg",))
+
+
+@pytest.mark.parametrize("n_src,n", [(1, 1), (1, 1000), (2, 1), (5, 3), (1000, 1), (70000, 2)])
+def test_small_and_degenerate(ctx, n_src, n):
+    for rec in (1, 4, 100):
+        src = synth.records(n_src, rec, n_src)
+        check(ctx, src, synth.uniform_ids(n, n_src, n))
+
+
+def test_empty(ctx):
+    src = to_dev(synth.records(10, 8, 1))
+    out = ctx.retrieve(src, torch.zeros(0, dtype=torch.int32, device=DEV))
+    ctx.retrieve_direct(src, torch.zeros(0, dtype=torch.int32, device=DEV))
+    ctx.sync()
+    assert out.shape == (0, 8)
+    empty = torch.zeros((0, 8), dtype=torch.uint8, device=DEV)
+    ctx.retrieve(empty, torch.zeros(0, dtype=torch.int32, device=DEV))
+    ctx.sync()
+
+
+@pytest.mark.parametrize("src_off,dst_off", [(1, 0), (0, 3), (4, 8), (8, 4), (2, 6), (16, 1)])
+def test_unaligned_tables(ctx, src_off, dst_off):
+    n_src, n = 9001, 12000
+    for rec in (16, 100, 64):
+        src = synth.records(n_src, rec, 5)
+        rids = synth.uniform_ids(n, n_src, 6)
+        want = oracle.retrieve(src, rids)
+        big = torch.zeros(n_src * rec + 64, dtype=torch.uint8, device=DEV)
+        d_src = big[src_off:src_off + n_src * rec].view(n_src, rec)
+        d_src.copy_(to_dev(src))
+        bigd = torch.zeros(n * rec + 64, dtype=torch.uint8, device=DEV)
+        d_dst = bigd[dst_off:dst_off + n * rec].view(n, rec)
+        for fn in (ctx.retrieve, ctx.retrieve_direct):
+            d_dst.fill_(0)
+            fn(d_src, to_dev(rids), out=d_dst)
+            ctx.sync()
+            assert np.array_equal(d_dst.cpu().numpy(), want)
+        # bytes around the destination untouched
+        assert int(bigd[:dst_off].sum()) == 0 and int(bigd[dst_off + n * rec:].sum()) == 0
+
+
+@pytest.mark.parametrize("bad", [-1, 5000, 2**31 - 1])
+def test_bad_rid_leaves_destination_untouched(ctx, bad):
+    from paper_cs_0308004_gb300 import dpg
+    n_src, rec = 5000, 100
+    src = to_dev(synth.records(n_src, rec, 1))
+    rids = synth.uniform_ids(20000, n_src, 2)
+    rids[12345] = bad
+    out = torch.full((rids.size, rec), 0x5A, dtype=torch.uint8, device=DEV)
+    ctx.retrieve(src, to_dev(rids), out=out)
+    with pytest.raises(dpg.DpgRangeError):
+        ctx.sync()
+    assert bool((out == 0x5A).all())
+    ctx.retrieve_direct(src, to_dev(rids), out=out)
+    with pytest.raises(dpg.DpgRangeError):
+        ctx.sync()
+    ctx.sync()  # the error was cleared
+    # an empty source table: every rid is out of range
+    empty = torch.zeros((0, rec), dtype=torch.uint8, device=DEV)
+    ctx.retrieve(empty, to_dev(np.zeros(3, np.int32)))
+    with pytest.raises(dpg.DpgRangeError):
+        ctx.sync()
+
+
+def test_argument_errors(ctx):
+    from paper_cs_0308004_gb300 import dpg
+    buf = torch.zeros(1000 * 10, dtype=torch.uint8, device=DEV)
+    src = buf[:5000].view(500, 10)
+    rids = torch.zeros(300, dtype=torch.int32, device=DEV)
+    with pytest.raises(dpg.DpgError):
+        ctx.retrieve(src, rids, out=buf[4000:7000].view(300, 10))   # overlaps src
+    with pytest.raises(dpg.DpgError):
+        ctx.retrieve(torch.zeros((5, 0), dtype=torch.uint8, device=DEV), rids[:0].clone(),
+                     out=torch.zeros((0, 0), dtype=torch.uint8, device=DEV))
+    with pytest.raises(ValueError):
+        ctx.retrieve(src.cpu(), rids)
+    with pytest.raises(dpg.DpgError):
+        ctx.retrieve(torch.zeros((2, 70000), dtype=torch.uint8, device=DEV), rids[:1].clone())
+
+
+def test_config1_full_size(ctx):
+    """1,000,000 records of 100 bytes, a random permutation: full comparison."""
+    src, rids = synth.plain_retrieval(1_000_000, 100, 1, 2)
+    check(ctx, src, rids)
+    check(ctx, src, synth.uniform_ids(1_000_000, 1_000_000, 5))
+
+
+# ------------------------------------------------------------ sort copy (§3)
+
+@pytest.mark.parametrize("rec", [16, 32, 64, 100, 256])
+def test_sort_copy_matches_oracle(ctx, rec):
+    n = 200_003
+    src = synth.sort_file(n, rec, 3)
+    pairs = oracle.sort_keyptr(src, 10)
+    want = oracle.sort_copy(pairs, src)
+    d_src, d_pairs = to_dev(src), to_dev(pairs)
+    for fn in (ctx.sort_copy, ctx.sort_copy_direct):
+        out = fn(d_pairs, d_src)
+        ctx.sync()
+        assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_sort_copy_other_pair_layouts(ctx):
+    n_src, rec = 30001, 24
+    src = synth.records(n_src, rec, 4)
+    rids = synth.uniform_ids(40000, n_src, 5)
+    want = oracle.retrieve(src, rids)
+    for stride, off in ((4, 0), (8, 4), (12, 0), (32, 20)):
+        pairs = np.zeros((rids.size, stride), np.uint8)
+        pairs[:, off:off + 4] = rids.astype("<i4").view(np.uint8).reshape(-1, 4)
+        for fn in (ctx.sort_copy, ctx.sort_copy_direct):
+            out = fn(to_dev(pairs), to_dev(src), rid_off=off)
+            ctx.sync()
+            assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_sort_copy_full_size_sampled(ctx):
+    """10,000,000 records of 100 bytes (1 GB), pairs sorted by the oracle:
+    sampled outputs against the oracle, plus the sortedness and permutation
+    properties on the whole output."""
+    n, rec = 10_000_000, 100
+    src = synth.sort_file(n, rec, 3)
+    pairs = oracle.sort_keyptr(src, 10)
+    d_src, d_pairs = to_dev(src), to_dev(pairs)
+    out = ctx.sort_copy(d_pairs, d_src)
+    ctx.sync()
+    idx = np.sort(synth.uniform_ids(50_000, n, 17)).astype(np.int64)
+    rids = oracle.pair_rids(pairs)
+    want = oracle.retrieve(src, rids[idx])
+    got = out[torch.from_numpy(idx).to(DEV)].cpu().numpy()
+    assert np.array_equal(got, want)
+    # properties over the full output: keys non-decreasing, same multiset of records
+    keys = out[:, :10].to(torch.int64)
+    parts = [(keys[:, a:b] * torch.tensor([256 ** (b - 1 - k) for k in range(a, b)], dtype=torch.int64,
+                                           device=DEV)).sum(1) for a, b in ((0, 3), (3, 7), (7, 10))]
+    ok = torch.zeros(n - 1, dtype=torch.bool, device=DEV)   # strictly greater somewhere, equal before
+    eq = torch.ones(n - 1, dtype=torch.bool, device=DEV)
+    for p in parts:
+        ok |= eq & (p[1:] > p[:-1])
+        eq &= p[1:] == p[:-1]
+    ok |= eq
+    assert bool(ok.all())
+    h = torch.arange(1, rec + 1, dtype=torch.int64, device=DEV) * 1000003
+    hs = (d_src.to(torch.int64) * h).sum(1).sort().values
+    ho = (out.to(torch.int64) * h).sum(1).sort().values
+    assert torch.equal(hs, ho)

@@ -140,6 +140,31 @@ size_t dpg_trace_count(dpg_ctx* ctx);
 dpg_status dpg_trace_get(dpg_ctx* ctx, size_t index, const char** name, double* total_ms,
                          uint64_t* launches);
 
+/*
+ * Allocation-free retrieval.  The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory at the time of the call (code
+ * running while a caching allocator holds all free memory, memory-capped or
+ * pre-budgeted regions, plug-ins that must not allocate after start-up).
+ *
+ * Same result as dpg_retrieve (dst[i] = src[rids[i]], computed by the 2-pass
+ * DPG plan), but it takes no context and allocates nothing: its scratch is a
+ * fixed ~17.6 MB array that the library reserves on every device it is loaded
+ * on, until the process exits.  Runs on the calling thread's current device;
+ * all pointers are device pointers on that device.
+ *   - Limits: n <= 2,097,152 rids, rec_bytes <= 65536, and at most 4096
+ *     source segments of up to 110 KB each (about 450 MB of source table);
+ *     beyond them it returns DPG_EINVAL and enqueues nothing.
+ *   - The first call on each device looks up the array's device address;
+ *     make that first call before any stream capture.
+ *   - The call is synchronous: it waits for `stream` and returns the final
+ *     status (DPG_ERANGE for a bad rid, destination untouched).
+ *   - Every call uses the same array (each call clears what must start at
+ *     zero): calls whose GPU work overlaps, from two streams or two host
+ *     threads, race and may return wrong data.
+ */
+dpg_status dpg_retrieve_noalloc(const void* src, size_t n_src, size_t rec_bytes, size_t n,
+                                const int32_t* rids, void* dst, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
+#include <type_traits>
 
 #include "dpg_device.cuh"
 #include "dpg_internal.h"
@@ -603,3 +605,181 @@ int run_direct(dpg_ctx& ctx, const Retrieval& r) {
 }
 
 }  // namespace dpg
+
+// ---------------------------------------------------------------------------
+// Allocation-free retrieval (dpg_retrieve_noalloc in include/dpg.h).
+//
+// Some callers cannot call cudaMalloc: code that runs while a caching
+// allocator owns all free device memory, code inside a memory-capped or
+// pre-budgeted region, or a plug-in loaded into a host process that forbids
+// device allocations after start-up.  For them this entry point runs the
+// 2-pass DPG plan (no INTERNAL staging table) with its scratch in one
+// fixed-size __device__ array that the CUDA module reserves on every device
+// the library is loaded on, for the life of the process.  It needs no
+// context, allocates nothing, and calls no allocating routine.
+//
+// Capacity: at most kNoallocMaxRids rids, at most kNoallocMaxSegs source
+// segments (about 450 MB of 100-byte records); larger requests return
+// DPG_EINVAL before anything is enqueued.  Every call shares the array, so
+// calls whose GPU work overlaps (two streams, two host threads) race.
+namespace dpg {
+namespace {
+
+constexpr uint64_t kNoallocMaxRids = 1ull << 21;
+constexpr uint32_t kNoallocMaxSegs = 4096;
+constexpr uint32_t kNoallocMaxCtas = 304;
+constexpr size_t kNaAl(size_t x) { return (x + 255) & ~size_t(255); }
+// byte offsets inside the array
+constexpr size_t kNaErr = 0;
+constexpr size_t kNaCounter = 256;
+constexpr size_t kNaTot = 512;
+constexpr size_t kNaOff = kNaTot + kNaAl(kNoallocMaxSegs * 4);
+constexpr size_t kNaItemoff = kNaOff + kNaAl((kNoallocMaxSegs + 1) * 4);
+constexpr size_t kNaTsum = kNaItemoff + kNaAl((kNoallocMaxSegs + 1) * 4);
+constexpr size_t kNaIsum = kNaTsum + 256;
+constexpr size_t kNaCnt = kNaIsum + 256;
+constexpr size_t kNaLo = kNaCnt + kNaAl((size_t)kNoallocMaxSegs * kNoallocMaxCtas * 4);
+constexpr size_t kNaDest = kNaLo + kNaAl(kNoallocMaxRids * 2);
+constexpr size_t kNoallocBytes = kNaDest + kNaAl(kNoallocMaxRids * 4);
+static_assert((kNoallocMaxSegs + kScanTile - 1) / kScanTile * 4 <= 256, "tile sums fit their slot");
+
+// The scratch itself: ~17.6 MB per device.  Host code must not use this name
+// as an address (it is a host-side stand-in); it asks the runtime for the
+// device address once per device instead.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kNoallocDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kNoallocDevices] = {};
+int g_noalloc_sms[kNoallocDevices] = {};
+
+// Device address of the array for the current device, looked up on the first
+// call made with that device current.
+int noalloc_setup(int dev, unsigned char** out, int* sms) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return DPG_ECUDA;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return DPG_ECUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    g_noalloc_sms[dev] = n;
+  }
+  *out = g_noalloc_ptr[dev];
+  *sms = g_noalloc_sms[dev];
+  return DPG_OK;
+}
+
+template <class Launch>
+int noalloc_probe(uint32_t wb, Launch&& go) {
+  switch (wb) {
+    case 16: go(std::integral_constant<int, 16>{}); break;
+    case 8: go(std::integral_constant<int, 8>{}); break;
+    case 4: go(std::integral_constant<int, 4>{}); break;
+    case 2: go(std::integral_constant<int, 2>{}); break;
+    default: go(std::integral_constant<int, 1>{}); break;
+  }
+  return DPG_OK;
+}
+
+}  // namespace
+}  // namespace dpg
+
+extern "C" dpg_status dpg_retrieve_noalloc(const void* src_v, size_t n_src, size_t rec, size_t n,
+                                           const int32_t* rids, void* dst_v, void* stream_v) {
+  using namespace dpg;
+  if (rec == 0 || rec > kMaxDpgRecBytes || n_src > 0x7fffffffULL) return DPG_EINVAL;
+  if (n == 0) return DPG_OK;
+  if (!rids || !dst_v || (n_src > 0 && !src_v)) return DPG_EINVAL;
+  if (n > kNoallocMaxRids) return DPG_EINVAL;
+  const uint8_t* src = static_cast<const uint8_t*>(src_v);
+  uint8_t* dst = static_cast<uint8_t*>(dst_v);
+  const uintptr_t s0 = reinterpret_cast<uintptr_t>(src), d0 = reinterpret_cast<uintptr_t>(dst),
+                  r0 = reinterpret_cast<uintptr_t>(rids);
+  if (n_src && s0 < d0 + n * rec && d0 < s0 + n_src * rec) return DPG_EINVAL;
+  if (r0 < d0 + n * rec && d0 < r0 + n * 4) return DPG_EINVAL;
+  int sl = 0;
+  while (sl < 16 && ((2ull << sl) * rec) <= kSegBytesMax) ++sl;
+  const uint64_t S = 1ull << sl;
+  const uint32_t nb = (uint32_t)((n_src + S - 1) >> sl);
+  if (nb > kNoallocMaxSegs) return DPG_EINVAL;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocDevices) {
+    cudaGetLastError();
+    return DPG_ECUDA;
+  }
+  unsigned char* base = nullptr;
+  int sms = 0;
+  if (int s = noalloc_setup(dev, &base, &sms)) return (dpg_status)s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream_v);
+  int* err = reinterpret_cast<int*>(base + kNaErr);
+  uint32_t* counter = reinterpret_cast<uint32_t*>(base + kNaCounter);
+  uint32_t* tot = reinterpret_cast<uint32_t*>(base + kNaTot);
+  uint32_t* off = reinterpret_cast<uint32_t*>(base + kNaOff);
+  uint32_t* itemoff = reinterpret_cast<uint32_t*>(base + kNaItemoff);
+  uint32_t* tsum = reinterpret_cast<uint32_t*>(base + kNaTsum);
+  uint32_t* isum = reinterpret_cast<uint32_t*>(base + kNaIsum);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(base + kNaCnt);
+  uint16_t* lo = reinterpret_cast<uint16_t*>(base + kNaLo);
+  uint32_t* dest = reinterpret_cast<uint32_t*>(base + kNaDest);
+
+  // the error word and the segment totals must start at zero on every call
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess && nb) e = cudaMemsetAsync(tot, 0, (size_t)nb * 4, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return DPG_ECUDA;
+  }
+  if (n_src == 0) {
+    k_flag_range<<<1, 1, 0, st>>>(err);
+  } else {
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>({(uint64_t)sms * 2, (uint64_t)kNoallocMaxCtas, (n + 8191) / 8192}));
+    const uint64_t per = (n + grid - 1) / grid;
+    const uint32_t chunk = (uint32_t)(4 * S);
+    const size_t phase_smem = (size_t)nb * 4;
+    RidArray rid{rids};
+    auto kh = k_hist<RidArray>;
+    set_smem(kh, phase_smem);
+    kh<<<grid, kPhaseThreads, phase_smem, st>>>(rid, n, (uint32_t)n_src, sl, nb, grid, per, cnt, tot, err, 1);
+    const uint32_t ntiles = (nb + kScanTile - 1) / kScanTile;
+    k_tile_sums<<<ntiles, kScanTile, 0, st>>>(tot, nb, chunk, tsum, isum, err);
+    k_scan<<<(nb + 31) / 32, 1024, 0, st>>>(tot, tsum, isum, nb, grid, chunk, cnt, off, itemoff, counter, err);
+    auto kd = k_distribute<RidArray, uint16_t, false>;
+    set_smem(kd, phase_smem);
+    kd<<<grid, kPhaseThreads, phase_smem, st>>>(rid, n, sl, nb, grid, per, cnt, lo, dest, err, 1);
+    const int use_bulk = (s0 % 16 == 0) && ((S * rec) % 16 == 0);
+    uint32_t wb = std::min(pow2_align(rec), pow2_align(d0));
+    if (!use_bulk) wb = std::min(wb, pow2_align(s0));
+    const uint32_t seg_bytes = (uint32_t)(std::min<uint64_t>(S, n_src) * rec);
+    const size_t probe_smem = ((size_t)seg_bytes + 15) & ~size_t(15);
+    noalloc_probe(wb, [&](auto wbc) {
+      constexpr int WBV = decltype(wbc)::value;
+      auto kp = k_probe<WBV, uint16_t, true>;
+      set_smem(kp, probe_smem);
+      const uint32_t W = (uint32_t)rec / WBV;
+      kp<<<sms * 2, kProbeThreads, probe_smem, st>>>(src, (uint32_t)n_src, (uint32_t)rec, sl, off, itemoff, nb,
+                                                      chunk, lo, dest, dst, W, make_fastdiv(W), err, counter,
+                                                      use_bulk);
+    });
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  int bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&bits, g_noalloc_scratch, sizeof(int), kNaErr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return DPG_ECUDA;
+  }
+  if (bits & ERR_RANGE) return DPG_ERANGE;
+  if (bits & ERR_TIMEOUT) return DPG_ETIMEOUT;
+  return DPG_OK;
+}

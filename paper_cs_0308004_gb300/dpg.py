@@ -42,6 +42,7 @@ SIGNATURES = {
     "dpg_trace_count": ([_P], _S),
     "dpg_trace_get": ([_P, _S, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                        ctypes.POINTER(ctypes.c_uint64)], _I),
+    "dpg_retrieve_noalloc": ([_P, _S, _S, _S, _P, _P, _P], _I),
 }
 
 

@@ -50,6 +50,9 @@ def args_():
     p.add_argument("--rec", type=int, default=100)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sweep", action="store_true",
+                   help="record-size sweep (16/32/64/100/256 B at 1e9 B of source each, permutation rids): "
+                        "one JSON line per size, DPG vs direct; not the headline run")
     return p.parse_args()
 
 
@@ -143,6 +146,7 @@ def per_kernel_bytes(n, n_src, rec, stride):
         "k_hist": n * stride,
         "k_distribute": n * stride + 2 * n + 4 * n,
         "k_probe": 2 * n + n_src * rec + n * rec,
+        "k_probe_scatter": 6 * n + n_src * rec + n * rec,
         "k_gather_phase3": 4 * n + 2 * n * rec,
         "k_gather_direct": n * stride + 2 * n * rec,
     }
@@ -165,8 +169,60 @@ def run_cpu_baseline(src, pairs, rec, budget_s=10.0):
             "sample": f"first {m} of {pairs.shape[0]} sorted pairs, {reps} repetitions, {t_total:.1f} s"}
 
 
+def run_sweep(a):
+    """DPG vs direct over the record sizes of the sort workload (1e9 bytes of
+    source each, rids a Fisher-Yates permutation: the access pattern of the
+    sort copy phase)."""
+    import torch
+    from paper_cs_0308004_gb300 import dpg
+    dev = torch.device("cuda", 0)
+    peak, peak_kind = hbm_peak()
+    ctx = dpg.Context(0)
+    stream = torch.cuda.current_stream(dev)
+    for rec in (16, 32, 64, 100, 256):
+        n = 10 ** 9 // rec
+        d_src = torch.from_numpy(synth.records(n, rec, 3)).to(dev)
+        rids = synth.permutation(n, 2)
+        d_rids = torch.from_numpy(rids).to(dev)
+        out = torch.empty((n, rec), dtype=torch.uint8, device=dev)
+        res = {}
+        for name, fn in (("dpg", ctx.retrieve), ("direct", ctx.retrieve_direct)):
+            for _ in range(a.warmup):
+                fn(d_src, d_rids, out=out)
+            ctx.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.steps):
+                fn(d_src, d_rids, out=out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ctx.sync()
+            res[name] = e0.elapsed_time(e1) / a.steps
+        idx = torch.randint(0, n, (4096,), device=dev)
+        assert torch.equal(out[idx], d_src[d_rids[idx].long()])
+        ctx.trace_reset()
+        ctx.trace(True)
+        for _ in range(3):
+            ctx.retrieve(d_src, d_rids, out=out)
+        torch.cuda.synchronize(dev)
+        kern = {k: round(v[0] / v[1] * 1e3, 1) for k, v in ctx.trace_read().items()}
+        ctx.trace(False)
+        b = n * (2 * rec + 4)
+        print(json.dumps({"impl": "sweep", "rec_bytes": rec, "n": n, "steps": a.steps,
+                          "dpg_gbs": round(b / res["dpg"] / 1e6, 1), "direct_gbs": round(b / res["direct"] / 1e6, 1),
+                          "dpg_ms": round(res["dpg"], 4), "direct_ms": round(res["direct"], 4),
+                          "dpg_pct_peak": round(b / res["dpg"] / 1e6 / peak, 4),
+                          "speedup_vs_direct": round(res["direct"] / res["dpg"], 4),
+                          "peak": peak, "peak_kind": peak_kind, "dpg_kernels_us": kern}), flush=True)
+        del d_src, d_rids, out
+        torch.cuda.empty_cache()
+    ctx.close()
+
+
 def main():
     a = args_()
+    if a.sweep:
+        return run_sweep(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

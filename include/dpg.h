@@ -152,7 +152,7 @@ dpg_status dpg_trace_get(dpg_ctx* ctx, size_t index, const char** name, double* 
  * on, until the process exits.  Runs on the calling thread's current device;
  * all pointers are device pointers on that device.
  *   - Limits: n <= 2,097,152 rids, rec_bytes <= 65536, and at most 4096
- *     source segments of up to 110 KB each (about 450 MB of source table);
+ *     source segments of up to 104 KB each (about 420 MB of 100-byte records);
  *     beyond them it returns DPG_EINVAL and enqueues nothing.
  *   - The first call on each device looks up the array's device address;
  *     make that first call before any stream capture.

@@ -35,9 +35,10 @@ constexpr int kGatherThreads = 256;
 constexpr int kGatherUnroll = 8;
 constexpr int kPhaseThreads = 1024;
 constexpr int kProbeThreads = 512;
-constexpr uint32_t kSegBytesMax = 110 * 1024;  // two probe CTAs per SM
+constexpr uint32_t kSegBytesMax = 104 * 1024;  // two probe CTAs per SM (segment + staged run entries)
 constexpr uint32_t kBulkPiece = 32 * 1024;     // bytes per cp.async.bulk request
 constexpr int kDistUnroll = 4;
+constexpr int kHistUnroll = 8;
 
 // --------------------------------------------------------------- K1 / K6
 // dst[i] = src[idx(i)] for i in [0, n).  The destination is one contiguous
@@ -84,13 +85,14 @@ __global__ void __launch_bounds__(kGatherThreads)
 
 // --------------------------------------------------------------------- K2
 // CTA g counts the rids of [g*per, (g+1)*per) per segment in shared memory and
-// writes its column of the bucket-major count matrix cnt[b*G + g]; tot[b]
-// accumulates the segment totals.  With more segments than shared counters
-// (smem_mode == 0) it counts straight into tot[] with global atomics.
+// writes its column of the bucket-major count matrix cnt[b*G + g].  With more
+// segments than shared counters (smem_mode == 0) it counts straight into the
+// segment totals tot[] with global atomics.
 template <class Rid>
 __global__ void __launch_bounds__(kPhaseThreads)
     k_hist(Rid rid, uint64_t n, uint32_t n_src, uint32_t seg_log2, uint32_t nb, uint32_t G, uint64_t per,
-           uint32_t* __restrict__ cnt, uint32_t* __restrict__ tot, int* err, int smem_mode) {
+           uint32_t* __restrict__ cnt, uint32_t* __restrict__ tot, int* err, int smem_mode,
+           int32_t* __restrict__ compact) {
   extern __shared__ uint32_t h[];
   const uint32_t g = blockIdx.x;
   if (smem_mode) {
@@ -99,17 +101,18 @@ __global__ void __launch_bounds__(kPhaseThreads)
   }
   const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
   bool bad = false;
-  for (uint64_t i0 = lo + threadIdx.x; i0 < hi; i0 += (uint64_t)kDistUnroll * blockDim.x) {
-    int32_t r[kDistUnroll];
+  for (uint64_t i0 = lo + threadIdx.x; i0 < hi; i0 += (uint64_t)kHistUnroll * blockDim.x) {
+    int32_t r[kHistUnroll];
 #pragma unroll
-    for (int k = 0; k < kDistUnroll; ++k) {
+    for (int k = 0; k < kHistUnroll; ++k) {
       const uint64_t i = i0 + (uint64_t)k * blockDim.x;
       r[k] = i < hi ? rid(i) : 0;
     }
 #pragma unroll
-    for (int k = 0; k < kDistUnroll; ++k) {
+    for (int k = 0; k < kHistUnroll; ++k) {
       const uint64_t i = i0 + (uint64_t)k * blockDim.x;
       if (i < hi) {
+        if (compact) compact[i] = r[k];
         if ((uint32_t)r[k] >= n_src) {
           bad = true;
         } else {
@@ -123,48 +126,54 @@ __global__ void __launch_bounds__(kPhaseThreads)
   if (bad) atomicOr(err, ERR_RANGE);
   if (smem_mode) {
     __syncthreads();
-    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
-      const uint32_t c = h[b];
-      cnt[(uint64_t)b * G + g] = c;
-      if (c) atomicAdd(&tot[b], c);
-    }
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cnt[(uint64_t)b * G + g] = h[b];
   }
 }
 
 // --------------------------------------------------------------------- K3
 constexpr uint32_t kScanTile = 1024;  // segments per tile of the two-level scan
 
-// K3a: per tile of kScanTile segments, the sum of the rid counts and of the
-// probe work items (ceil(count / chunk)).
+// K3a: block x owns segments [32x, 32x+32), one warp per segment.  In
+// shared-counter mode each warp sums its row of the count matrix into tot[b];
+// the block then adds its segments' rid counts and probe work items
+// (ceil(count / chunk)) to the sums of their tile of kScanTile segments
+// (tsum, isum: zeroed before the launch).
 __global__ void __launch_bounds__(1024)
-    k_tile_sums(const uint32_t* __restrict__ tot, uint32_t nb, uint32_t chunk, uint32_t* __restrict__ tsum,
-                uint32_t* __restrict__ isum, const int* err) {
+    k_bucket_totals(const uint32_t* __restrict__ cnt, uint32_t* __restrict__ tot, uint32_t nb, uint32_t G,
+                    uint32_t chunk, uint32_t* __restrict__ tsum, uint32_t* __restrict__ isum, const int* err,
+                    int smem_mode) {
   __shared__ uint32_t s_t[32], s_i[32];
   if (error_set(err)) return;
-  const uint32_t b = blockIdx.x * kScanTile + threadIdx.x;
-  uint32_t t = b < nb ? tot[b] : 0, it = (t + chunk - 1) / chunk;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    t += __shfl_xor_sync(0xffffffffu, t, o);
-    it += __shfl_xor_sync(0xffffffffu, it, o);
-  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t b = blockIdx.x * 32 + warp;
+  uint32_t t = 0;
+  if (b < nb) {
+    if (smem_mode) {
+      const uint32_t* row = cnt + (uint64_t)b * G;
+      for (uint32_t c = lane; c < G; c += 32) t += row[c];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) tot[b] = t;
+    } else {
+      t = tot[b];
+    }
+  }
   if (lane == 0) {
     s_t[warp] = t;
-    s_i[warp] = it;
+    s_i[warp] = (t + chunk - 1) / chunk;
   }
   __syncthreads();
   if (warp == 0) {
-    t = s_t[lane];
-    it = s_i[lane];
+    uint32_t x = s_t[lane], y = s_i[lane];
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-      t += __shfl_xor_sync(0xffffffffu, t, o);
-      it += __shfl_xor_sync(0xffffffffu, it, o);
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
     }
     if (lane == 0) {
-      tsum[blockIdx.x] = t;
-      isum[blockIdx.x] = it;
+      const uint32_t tile = blockIdx.x * 32 / kScanTile;
+      atomicAdd(&tsum[tile], x);
+      atomicAdd(&isum[tile], y);
     }
   }
 }
@@ -257,9 +266,9 @@ __global__ void __launch_bounds__(1024)
 // CTA g re-reads the rids of [g*per, (g+1)*per) and appends each one's offset
 // inside its segment to that segment's run at the CTA's cursor.  SLOT: the
 // 3-pass plan records slot[i] = run position of rid i; otherwise the 2-pass
-// plan records dest[pos] = i.  Rids are taken in sub-tiles separated by a
-// barrier, so within a run the entries of one CTA keep rid order up to
-// reordering inside a sub-tile of kDistUnroll * blockDim rids.
+// plan records dest[pos] = i.  The entries one CTA adds to a run occupy the
+// contiguous range the scan reserved for it; their order inside that range is
+// not fixed (the result does not depend on it: every entry carries its slot).
 template <class Rid, typename LoT, bool SLOT>
 __global__ void __launch_bounds__(kPhaseThreads)
     k_distribute(Rid rid, uint64_t n, uint32_t seg_log2, uint32_t nb, uint32_t G, uint64_t per,
@@ -274,23 +283,16 @@ __global__ void __launch_bounds__(kPhaseThreads)
   }
   const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
   const uint32_t mask = (1u << seg_log2) - 1u;
-  const uint64_t tile = (uint64_t)kDistUnroll * blockDim.x;
-  int32_t r[kDistUnroll];
+  for (uint64_t i0 = lo + threadIdx.x; i0 < hi; i0 += (uint64_t)kHistUnroll * blockDim.x) {
+    int32_t r[kHistUnroll];
 #pragma unroll
-  for (int k = 0; k < kDistUnroll; ++k) {
-    const uint64_t i = lo + (uint64_t)k * blockDim.x + threadIdx.x;
-    r[k] = i < hi ? rid(i) : 0;
-  }
-  for (uint64_t t0 = lo; t0 < hi; t0 += tile) {
-    int32_t nr[kDistUnroll];
-#pragma unroll
-    for (int k = 0; k < kDistUnroll; ++k) {
-      const uint64_t i = t0 + tile + (uint64_t)k * blockDim.x + threadIdx.x;
-      nr[k] = i < hi ? rid(i) : 0;
+    for (int k = 0; k < kHistUnroll; ++k) {
+      const uint64_t i = i0 + (uint64_t)k * blockDim.x;
+      r[k] = i < hi ? rid(i) : 0;
     }
 #pragma unroll
-    for (int k = 0; k < kDistUnroll; ++k) {
-      const uint64_t i = t0 + (uint64_t)k * blockDim.x + threadIdx.x;
+    for (int k = 0; k < kHistUnroll; ++k) {
+      const uint64_t i = i0 + (uint64_t)k * blockDim.x;
       if (i < hi) {
         const uint32_t rv = (uint32_t)r[k];
         const uint32_t b = rv >> seg_log2;
@@ -300,28 +302,42 @@ __global__ void __launch_bounds__(kPhaseThreads)
         else side[pos] = (uint32_t)i;
       }
     }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kDistUnroll; ++k) r[k] = nr[k];
   }
 }
 
 // ------------------------------------------------------------------ K5/K7
 // Persistent CTAs take work items (segment b, chunk c) from a global counter.
 // A new segment is copied into shared memory with cp.async.bulk (16-byte
-// aligned source) or with plain vector loads; then the chunk's run entries
-// [p0, p1) are served from shared memory: word w of entry k is copied to
-// out[k] (INTERNAL staging, 3-pass) or to out[dest[k]] (the destination, 2-pass).
+// aligned source) or with plain vector loads.  The chunk's run entries are
+// then served kProbeSub at a time: their in-segment offsets (and, 2-pass,
+// destination slots) are staged in shared memory while the bulk copy is in
+// flight, and word w of entry k is copied from the segment to out[k]
+// (INTERNAL staging, 3-pass, written as one contiguous stream in 16-byte
+// vectors) or to out[dest[k]] (the destination, 2-pass).
+constexpr uint32_t kProbeSub = 1024;
+
+__device__ __forceinline__ uint4 pack16(const uint32_t (&x)[4]) { return make_uint4(x[0], x[1], x[2], x[3]); }
+__device__ __forceinline__ uint4 pack16(const uint2 (&x)[2]) { return make_uint4(x[0].x, x[0].y, x[1].x, x[1].y); }
+
+template <int WB, typename LoT>
+__device__ __forceinline__ typename WordT<WB>::T probe_word(const typename WordT<WB>::T* sw, const LoT* lo_s,
+                                                             uint32_t q, uint32_t w, uint32_t W) {
+  return sw[(uint32_t)lo_s[q] * W + w];
+}
+
 template <int WB, typename LoT, bool SCATTER>
 __global__ void __launch_bounds__(kProbeThreads)
     k_probe(const uint8_t* __restrict__ src, uint32_t n_src, uint32_t rec, uint32_t seg_log2,
             const uint32_t* __restrict__ off, const uint32_t* __restrict__ itemoff, uint32_t nb, uint32_t chunk,
             const LoT* __restrict__ lo, const uint32_t* __restrict__ dest, uint8_t* __restrict__ out, uint32_t W,
-            FastDiv fdW, int* err, uint32_t* item_counter, int use_bulk) {
+            FastDiv fdW, int* err, uint32_t* item_counter, int use_bulk, uint32_t seg_smem) {
   using T = typename WordT<WB>::T;
-  extern __shared__ __align__(128) uint8_t seg[];
+  extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t s_item, s_b;
+  uint8_t* seg = smem;
+  LoT* lo_s = reinterpret_cast<LoT*>(smem + seg_smem);
+  uint32_t* dest_s = reinterpret_cast<uint32_t*>(smem + seg_smem + kProbeSub * sizeof(LoT));
   if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
@@ -351,6 +367,7 @@ __global__ void __launch_bounds__(kProbeThreads)
     const uint32_t item = s_item;
     if (item >= n_items) break;
     const uint32_t b = s_b;
+    bool wait_bulk = false;
     if ((int64_t)b != loaded) {
       const uint64_t first = (uint64_t)b << seg_log2;
       const uint64_t left = (uint64_t)n_src - first;
@@ -365,38 +382,78 @@ __global__ void __launch_bounds__(kProbeThreads)
           for (uint32_t o = 0; o < body; o += kBulkPiece) bulk_g2s(seg + o, gsrc + o, min(kBulkPiece, body - o), &bar);
         }
         for (uint32_t o = body + threadIdx.x; o < bytes; o += blockDim.x) seg[o] = gsrc[o];
-        if (body) {
-          const bool ok = mbar_wait_bounded(&bar, phase);
-          if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) {
-              atomicOr(err, ERR_TIMEOUT);
-              mbar_wait_bounded(&bar, phase);  // let the copy in flight land before exiting
-            }
-            return;
-          }
-          phase ^= 1u;
-        }
+        wait_bulk = body != 0;
       } else {
         const T* gw = reinterpret_cast<const T*>(gsrc);
         T* sd = reinterpret_cast<T*>(seg);
         for (uint32_t o = threadIdx.x; o < bytes / WB; o += blockDim.x) sd[o] = gw[o];
       }
-      __syncthreads();
       loaded = b;
     }
     const uint32_t p0 = off[b] + (item - itemoff[b]) * chunk;
     const uint32_t p1 = min(off[b + 1], p0 + chunk);
-    const uint64_t total = (uint64_t)(p1 - p0) * W;
-    for (uint64_t t = threadIdx.x; t < total; t += blockDim.x) {
-      const uint64_t q = fdiv(t, fdW);
-      const uint32_t w = (uint32_t)(t - q * W);
-      const uint64_t k = p0 + q;
-      const T v = sw[(uint64_t)lo[k] * W + w];
-      if (SCATTER) ow[(uint64_t)dest[k] * W + w] = v;
-      else ow[k * W + w] = v;
+    for (uint32_t q0 = p0; q0 < p1; q0 += kProbeSub) {
+      const uint32_t nq = min(kProbeSub, p1 - q0);
+      for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
+        lo_s[q] = lo[q0 + q];
+        if (SCATTER) dest_s[q] = dest[q0 + q];
+      }
+      if (wait_bulk) {
+        const bool ok = mbar_wait_bounded(&bar, phase);
+        if (__syncthreads_or(!ok)) {
+          if (threadIdx.x == 0) {
+            atomicOr(err, ERR_TIMEOUT);
+            mbar_wait_bounded(&bar, phase);  // let the copy in flight land before exiting
+          }
+          return;
+        }
+        phase ^= 1u;
+        wait_bulk = false;
+      }
+      __syncthreads();
+      const uint64_t total = (uint64_t)nq * W;
+      if constexpr (SCATTER || WB >= 16 || WB <= 2) {
+        for (uint64_t t = threadIdx.x; t < total; t += blockDim.x) {
+          const uint32_t q = (uint32_t)fdiv(t, fdW);
+          const uint32_t w = (uint32_t)(t - (uint64_t)q * W);
+          const T v = probe_word<WB>(sw, lo_s, q, w, W);
+          if (SCATTER) ow[(uint64_t)dest_s[q] * W + w] = v;
+          else ow[(uint64_t)(q0 + q) * W + w] = v;
+        }
+      } else {
+        // contiguous output: 16-byte vectors of VEC words, scalar head and tail
+        constexpr uint32_t VEC = 16 / WB;
+        const uint64_t g0 = (uint64_t)q0 * W, g1 = g0 + total;
+        const uint64_t v0 = (g0 + VEC - 1) / VEC, v1 = g1 / VEC;
+        const uint64_t head_end = v0 * VEC < g1 ? v0 * VEC : g1;
+        for (uint64_t g = g0 + threadIdx.x; g < head_end; g += blockDim.x) {
+          const uint32_t q = (uint32_t)fdiv(g - g0, fdW);
+          ow[g] = probe_word<WB>(sw, lo_s, q, (uint32_t)(g - g0 - (uint64_t)q * W), W);
+        }
+        for (uint64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+          const uint64_t rel = v * VEC - g0;
+          uint32_t q = (uint32_t)fdiv(rel, fdW);
+          uint32_t w = (uint32_t)(rel - (uint64_t)q * W);
+          T x[VEC];
+#pragma unroll
+          for (uint32_t j = 0; j < VEC; ++j) {
+            x[j] = probe_word<WB>(sw, lo_s, q, w, W);
+            if (++w == W) {
+              w = 0;
+              ++q;
+            }
+          }
+          reinterpret_cast<uint4*>(out)[v] = pack16(x);
+        }
+        const uint64_t tail_start = v1 * VEC > head_end ? v1 * VEC : head_end;
+        for (uint64_t g = tail_start + threadIdx.x; g < g1; g += blockDim.x) {
+          const uint32_t q = (uint32_t)fdiv(g - g0, fdW);
+          ow[g] = probe_word<WB>(sw, lo_s, q, (uint32_t)(g - g0 - (uint64_t)q * W), W);
+        }
+      }
+      fence_proxy_async_smem();  // order this CTA's shared-memory accesses before the next bulk copy
+      __syncthreads();
     }
-    fence_proxy_async_smem();  // order this CTA's shared-memory accesses before the next bulk copy
-    __syncthreads();
   }
 }
 
@@ -444,17 +501,20 @@ void launch_gather(dpg_ctx& ctx, uint32_t WB, const uint8_t* src, uint8_t* dst, 
 template <typename LoT, bool SCATTER>
 void launch_probe(dpg_ctx& ctx, uint32_t WB, const Retrieval& r, uint32_t seg_log2, const uint32_t* off,
                   const uint32_t* itemoff, uint32_t nb, uint32_t chunk, const LoT* lo, const uint32_t* dest,
-                  uint8_t* out, uint32_t* counter, int use_bulk, size_t smem) {
+                  uint8_t* out, uint32_t* counter, int use_bulk, size_t seg_smem) {
   const uint32_t W = r.rec / WB;
+  const size_t smem = seg_smem + kProbeSub * sizeof(LoT) + (SCATTER ? kProbeSub * 4 : 0);
+  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024 + 256)));
   const FastDiv f = make_fastdiv(W);
-  const int grid = ctx.sms * 2;
+  const int grid = ctx.sms * per_sm;
   TraceScope ts(ctx, SCATTER ? "k_probe_scatter" : "k_probe", r.stream);
 #define DPG_PROBE(WBV)                                                                                         \
   {                                                                                                            \
     auto kern = k_probe<WBV, LoT, SCATTER>;                                                                    \
     set_smem(kern, smem);                                                                                      \
     kern<<<grid, kProbeThreads, smem, r.stream>>>(r.src, (uint32_t)r.n_src, r.rec, seg_log2, off, itemoff, nb, \
-                                                 chunk, lo, dest, out, W, f, ctx.d_err, counter, use_bulk);    \
+                                                 chunk, lo, dest, out, W, f, ctx.d_err, counter, use_bulk,     \
+                                                 (uint32_t)seg_smem);                                          \
   }
   switch (WB) {
     case 16: DPG_PROBE(16) break;
@@ -485,8 +545,10 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   const size_t b_cnt = al((size_t)nb * G * 4), b_tot = al((size_t)nb * 4), b_off = al(((size_t)nb + 1) * 4);
   const size_t b_ctr = 256, b_lo = al(r.n * sizeof(LoT)), b_side = al(r.n * 4);
   const size_t b_ts = al((size_t)((nb + kScanTile - 1) / kScanTile) * 4);
+  const bool strided = !std::is_same<Rid, RidArray>::value;
+  const size_t b_rc = strided ? al(r.n * 4) : 0;  // rids copied out of strided pairs by Phase I pass 1
   const size_t b_stage = three ? al(r.n * r.rec) : 0;
-  const size_t need = b_cnt + b_tot + 2 * b_off + b_ctr + 2 * b_ts + b_lo + b_side + b_stage;
+  const size_t need = b_cnt + b_tot + 2 * b_off + b_ctr + 2 * b_ts + b_lo + b_side + b_rc + b_stage;
   if (int s = ensure_scratch(ctx, need)) return s;
   uint8_t* p = static_cast<uint8_t*>(ctx.scratch);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(p); p += b_cnt;
@@ -498,9 +560,11 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   uint32_t* isum = reinterpret_cast<uint32_t*>(p); p += b_ts;
   LoT* lo = reinterpret_cast<LoT*>(p); p += b_lo;
   uint32_t* side = reinterpret_cast<uint32_t*>(p); p += b_side;
+  int32_t* rc = strided ? reinterpret_cast<int32_t*>(p) : nullptr; p += b_rc;
   uint8_t* stage = three ? p : nullptr;
 
-  cudaError_t e = cudaMemsetAsync(tot, 0, (size_t)nb * 4, r.stream);
+  cudaError_t e = smem_mode ? cudaSuccess : cudaMemsetAsync(tot, 0, (size_t)nb * 4, r.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tsum, 0, 2 * b_ts, r.stream);  // tsum, isum
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   const size_t phase_smem = smem_mode ? (size_t)nb * 4 : 0;
   {
@@ -508,13 +572,13 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
     auto kern = k_hist<Rid>;
     set_smem(kern, phase_smem);
     kern<<<grid, kPhaseThreads, phase_smem, r.stream>>>(rid, r.n, (uint32_t)r.n_src, sl, nb, G, per, cnt, tot,
-                                                        ctx.d_err, smem_mode);
+                                                        ctx.d_err, smem_mode, rc);
     ctx.launches++;
   }
-  const uint32_t ntiles = (nb + kScanTile - 1) / kScanTile;
   {
-    TraceScope ts(ctx, "k_tile_sums", r.stream);
-    k_tile_sums<<<ntiles, kScanTile, 0, r.stream>>>(tot, nb, chunk, tsum, isum, ctx.d_err);
+    TraceScope ts(ctx, "k_bucket_totals", r.stream);
+    k_bucket_totals<<<(nb + 31) / 32, 1024, 0, r.stream>>>(cnt, tot, nb, G, chunk, tsum, isum, ctx.d_err,
+                                                           smem_mode);
   }
   {
     TraceScope ts(ctx, "k_scan", r.stream);
@@ -524,9 +588,10 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   ctx.launches += 2;
   {
     TraceScope ts(ctx, "k_distribute", r.stream);
-    auto kern = three ? k_distribute<Rid, LoT, true> : k_distribute<Rid, LoT, false>;
+    const RidArray ra{strided ? rc : reinterpret_cast<const int32_t*>(r.rids.base)};
+    auto kern = three ? k_distribute<RidArray, LoT, true> : k_distribute<RidArray, LoT, false>;
     set_smem(kern, phase_smem);
-    kern<<<grid, kPhaseThreads, phase_smem, r.stream>>>(rid, r.n, sl, nb, G, per, cnt, lo, side, ctx.d_err,
+    kern<<<grid, kPhaseThreads, phase_smem, r.stream>>>(ra, r.n, sl, nb, G, per, cnt, lo, side, ctx.d_err,
                                                         smem_mode);
     ctx.launches++;
   }
@@ -619,7 +684,7 @@ int run_direct(dpg_ctx& ctx, const Retrieval& r) {
 // context, allocates nothing, and calls no allocating routine.
 //
 // Capacity: at most kNoallocMaxRids rids, at most kNoallocMaxSegs source
-// segments (about 450 MB of 100-byte records); larger requests return
+// segments (about 420 MB of 100-byte records); larger requests return
 // DPG_EINVAL before anything is enqueued.  Every call shares the array, so
 // calls whose GPU work overlaps (two streams, two host threads) race.
 namespace dpg {
@@ -731,9 +796,9 @@ extern "C" dpg_status dpg_retrieve_noalloc(const void* src_v, size_t n_src, size
   uint16_t* lo = reinterpret_cast<uint16_t*>(base + kNaLo);
   uint32_t* dest = reinterpret_cast<uint32_t*>(base + kNaDest);
 
-  // the error word and the segment totals must start at zero on every call
+  // the error word and the tile sums must start at zero on every call
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
-  if (e == cudaSuccess && nb) e = cudaMemsetAsync(tot, 0, (size_t)nb * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tsum, 0, 512, st);  // tsum and isum, adjacent
   if (e != cudaSuccess) {
     cudaGetLastError();
     return DPG_ECUDA;
@@ -749,9 +814,9 @@ extern "C" dpg_status dpg_retrieve_noalloc(const void* src_v, size_t n_src, size
     RidArray rid{rids};
     auto kh = k_hist<RidArray>;
     set_smem(kh, phase_smem);
-    kh<<<grid, kPhaseThreads, phase_smem, st>>>(rid, n, (uint32_t)n_src, sl, nb, grid, per, cnt, tot, err, 1);
-    const uint32_t ntiles = (nb + kScanTile - 1) / kScanTile;
-    k_tile_sums<<<ntiles, kScanTile, 0, st>>>(tot, nb, chunk, tsum, isum, err);
+    kh<<<grid, kPhaseThreads, phase_smem, st>>>(rid, n, (uint32_t)n_src, sl, nb, grid, per, cnt, tot, err, 1,
+                                                 nullptr);
+    k_bucket_totals<<<(nb + 31) / 32, 1024, 0, st>>>(cnt, tot, nb, grid, chunk, tsum, isum, err, 1);
     k_scan<<<(nb + 31) / 32, 1024, 0, st>>>(tot, tsum, isum, nb, grid, chunk, cnt, off, itemoff, counter, err);
     auto kd = k_distribute<RidArray, uint16_t, false>;
     set_smem(kd, phase_smem);
@@ -764,11 +829,12 @@ extern "C" dpg_status dpg_retrieve_noalloc(const void* src_v, size_t n_src, size
     noalloc_probe(wb, [&](auto wbc) {
       constexpr int WBV = decltype(wbc)::value;
       auto kp = k_probe<WBV, uint16_t, true>;
-      set_smem(kp, probe_smem);
+      const size_t smem = probe_smem + kProbeSub * (2 + 4);
+      set_smem(kp, smem);
       const uint32_t W = (uint32_t)rec / WBV;
-      kp<<<sms * 2, kProbeThreads, probe_smem, st>>>(src, (uint32_t)n_src, (uint32_t)rec, sl, off, itemoff, nb,
-                                                      chunk, lo, dest, dst, W, make_fastdiv(W), err, counter,
-                                                      use_bulk);
+      kp<<<sms * 2, kProbeThreads, smem, st>>>(src, (uint32_t)n_src, (uint32_t)rec, sl, off, itemoff, nb, chunk,
+                                                lo, dest, dst, W, make_fastdiv(W), err, counter, use_bulk,
+                                                (uint32_t)probe_smem);
     });
   }
   e = cudaGetLastError();

@@ -50,6 +50,8 @@ def args_():
     p.add_argument("--rec", type=int, default=100)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sweep-recs", default="16,32,64,100,256", help="record sizes of --sweep")
+    p.add_argument("--sweep-impls", default="dpg_smem,dpg_l2,direct", help="implementations of --sweep")
     p.add_argument("--sweep", action="store_true",
                    help="record-size sweep (16/32/64/100/256 B at 1e9 B of source each, permutation rids): "
                         "one JSON line per size, DPG vs direct; not the headline run")
@@ -179,14 +181,19 @@ def run_sweep(a):
     peak, peak_kind = hbm_peak()
     ctx = dpg.Context(0)
     stream = torch.cuda.current_stream(dev)
-    for rec in (16, 32, 64, 100, 256):
+    for rec in [int(x) for x in a.sweep_recs.split(",")]:
         n = 10 ** 9 // rec
         d_src = torch.from_numpy(synth.records(n, rec, 3)).to(dev)
         rids = synth.permutation(n, 2)
         d_rids = torch.from_numpy(rids).to(dev)
         out = torch.empty((n, rec), dtype=torch.uint8, device=dev)
-        res = {}
-        for name, fn in (("dpg", ctx.retrieve), ("direct", ctx.retrieve_direct)):
+        res, kern = {}, {}
+        for name, variant, fn in (("dpg_smem", "3", ctx.retrieve), ("dpg_l2", "4", ctx.retrieve),
+                                  ("direct", None, ctx.retrieve_direct)):
+            if name not in a.sweep_impls.split(","):
+                continue
+            if variant:
+                os.environ["DPG_VARIANT"] = variant
             for _ in range(a.warmup):
                 fn(d_src, d_rids, out=out)
             ctx.sync()
@@ -198,22 +205,27 @@ def run_sweep(a):
             torch.cuda.synchronize(dev)
             ctx.sync()
             res[name] = e0.elapsed_time(e1) / a.steps
-        idx = torch.randint(0, n, (4096,), device=dev)
-        assert torch.equal(out[idx], d_src[d_rids[idx].long()])
-        ctx.trace_reset()
-        ctx.trace(True)
-        for _ in range(3):
-            ctx.retrieve(d_src, d_rids, out=out)
-        torch.cuda.synchronize(dev)
-        kern = {k: round(v[0] / v[1] * 1e3, 1) for k, v in ctx.trace_read().items()}
-        ctx.trace(False)
+            idx = torch.randint(0, n, (4096,), device=dev)
+            assert torch.equal(out[idx], d_src[d_rids[idx].long()])
+            if variant:
+                ctx.trace_reset()
+                ctx.trace(True)
+                for _ in range(3):
+                    fn(d_src, d_rids, out=out)
+                torch.cuda.synchronize(dev)
+                kern[name] = {k: round(v[0] / v[1] * 1e3, 1) for k, v in ctx.trace_read().items()}
+                ctx.trace(False)
+        os.environ.pop("DPG_VARIANT", None)
         b = n * (2 * rec + 4)
-        print(json.dumps({"impl": "sweep", "rec_bytes": rec, "n": n, "steps": a.steps,
-                          "dpg_gbs": round(b / res["dpg"] / 1e6, 1), "direct_gbs": round(b / res["direct"] / 1e6, 1),
-                          "dpg_ms": round(res["dpg"], 4), "direct_ms": round(res["direct"], 4),
-                          "dpg_pct_peak": round(b / res["dpg"] / 1e6 / peak, 4),
-                          "speedup_vs_direct": round(res["direct"] / res["dpg"], 4),
-                          "peak": peak, "peak_kind": peak_kind, "dpg_kernels_us": kern}), flush=True)
+        line = {"impl": "sweep", "rec_bytes": rec, "n": n, "steps": a.steps, "peak": peak, "peak_kind": peak_kind}
+        for name, ms in res.items():
+            line[f"{name}_gbs"] = round(b / ms / 1e6, 1)
+            line[f"{name}_ms"] = round(ms, 4)
+        for name in ("dpg_smem", "dpg_l2"):
+            if name in res and "direct" in res:
+                line[f"{name}_speedup_vs_direct"] = round(res["direct"] / res[name], 4)
+        line["kernels_us"] = kern
+        print(json.dumps(line), flush=True)
         del d_src, d_rids, out
         torch.cuda.empty_cache()
     ctx.close()

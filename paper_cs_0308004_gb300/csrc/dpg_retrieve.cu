@@ -457,6 +457,155 @@ __global__ void __launch_bounds__(kProbeThreads)
   }
 }
 
+// ------------------------------------------------------- L2-run plan (variant 4)
+// The paper sizes a run to half the cache (Figure 1, L = CACHE_SIZE/2).  On
+// GB300 the cache that many SMs share is the 126 MB L2, so this plan uses runs
+// of ~16 MB of source: Phase I partitions the rids into a few dozen runs with
+// coalesced writes, Phase II gathers each run's records in run order while the
+// run is L2-resident (the source is prefetched into L2 sequentially, one run
+// ahead), and Phase III is the same slot gather as the 3-pass plan.
+
+constexpr uint32_t kPartMaxRuns = 1024;
+constexpr int kPartItems = 4;  // rids per thread per tile
+
+// K4': CTA g partitions the rids of [g*per, (g+1)*per) tile by tile.  Each tile
+// is counting-sorted by run in shared memory, then written to the runs as
+// contiguous pieces (run_rid[pos] = rid), and slot[i] = pos is written in rid
+// order.  The CTA's pieces of run b start at the cursor the scan reserved.
+template <class Rid>
+__global__ void __launch_bounds__(kPhaseThreads)
+    k_partition(Rid rid, uint64_t n, uint32_t seg_log2, uint32_t nb, uint32_t G, uint64_t per,
+                const uint32_t* __restrict__ cur_g, uint32_t* __restrict__ run_rid, uint32_t* __restrict__ slot,
+                const int* err) {
+  constexpr uint32_t T = kPartItems * kPhaseThreads;
+  __shared__ uint32_t cur[kPartMaxRuns], tcnt[kPartMaxRuns], toff[kPartMaxRuns], tfill[kPartMaxRuns];
+  __shared__ uint32_t ent[T];
+  __shared__ uint16_t ent_b[T];
+  __shared__ uint32_t s_warp[32];
+  if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
+  const uint32_t g = blockIdx.x;
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cur[b] = cur_g[(uint64_t)b * G + g];
+  const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t t0 = lo; t0 < hi; t0 += T) {
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+      tcnt[b] = 0;
+      tfill[b] = 0;
+    }
+    __syncthreads();
+    uint32_t r[kPartItems], bk[kPartItems];
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) {
+      const uint64_t i = t0 + (uint64_t)k * blockDim.x + threadIdx.x;
+      r[k] = i < hi ? (uint32_t)rid(i) : 0u;
+      bk[k] = r[k] >> seg_log2;
+      if (i < hi) atomicAdd(&tcnt[bk[k]], 1u);
+    }
+    __syncthreads();
+    // exclusive scan of tcnt[0, nb) (nb <= blockDim)
+    {
+      const uint32_t v = threadIdx.x < nb ? tcnt[threadIdx.x] : 0u;
+      uint32_t x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_warp[warp] = x;
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t w = s_warp[lane], z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+          if (lane >= o) z += y;
+        }
+        s_warp[lane] = z - w;
+      }
+      __syncthreads();
+      if (threadIdx.x < nb) toff[threadIdx.x] = s_warp[warp] + x - v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) {
+      const uint64_t i = t0 + (uint64_t)k * blockDim.x + threadIdx.x;
+      if (i < hi) {
+        const uint32_t p = toff[bk[k]] + atomicAdd(&tfill[bk[k]], 1u);
+        ent[p] = r[k];
+        ent_b[p] = (uint16_t)bk[k];
+        slot[i] = cur[bk[k]] + (p - toff[bk[k]]);
+      }
+    }
+    __syncthreads();
+    const uint32_t tn = (uint32_t)((hi - t0) < T ? (hi - t0) : T);
+    for (uint32_t p = threadIdx.x; p < tn; p += blockDim.x) {
+      const uint32_t b = ent_b[p];
+      run_rid[cur[b] + (p - toff[b])] = ent[p];
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cur[b] += tcnt[b];
+    __syncthreads();
+  }
+}
+
+// K5': INTERNAL[k] = src[run_rid[k]] in run order (the runs are consecutive
+// ranges of k).  Before each grid-stride step, thread 0 of every CTA claims
+// prefetch slices (kPfSlice bytes of source, in address order) up to the end
+// of the run after the one its next records fall in, so each run streams into
+// L2 sequentially just ahead of the random reads that probe it.
+constexpr uint32_t kPfSlice = 256 * 1024;
+
+template <int WB>
+__global__ void __launch_bounds__(kGatherThreads)
+    k_probe_l2(const uint8_t* __restrict__ src, uint8_t* __restrict__ out, const uint32_t* __restrict__ run_rid,
+               uint64_t n, uint32_t W, FastDiv fdW, const uint32_t* __restrict__ off, uint32_t nb,
+               uint64_t run_bytes, uint64_t src_bytes, uint32_t* pf_counter, int use_pf, const int* err) {
+  using T = typename WordT<WB>::T;
+  if (error_set(err)) return;
+  const T* s = reinterpret_cast<const T*>(src);
+  T* d = reinterpret_cast<T*>(out);
+  const uint64_t total = n * W;
+  const uint64_t step = (uint64_t)gridDim.x * kGatherThreads * kGatherUnroll;
+  const uint32_t n_slices = (uint32_t)((src_bytes + kPfSlice - 1) / kPfSlice);
+  for (uint64_t base = (uint64_t)blockIdx.x * kGatherThreads * kGatherUnroll + threadIdx.x; base < total;
+       base += step) {
+    if (use_pf && threadIdx.x == 0) {
+      // run of the records this CTA reaches one step from now
+      const uint64_t k_next = min(total - 1, base + step) / W;
+      uint32_t a = 0, z = nb;  // last run b with off[b] <= k_next
+      while (a < z) {
+        const uint32_t m = (a + z + 1) >> 1;
+        if (off[m] <= k_next) a = m;
+        else z = m - 1;
+      }
+      const uint64_t limit = min(src_bytes, (uint64_t)(a + 2) * run_bytes);
+      for (int claim = 0; claim < 2; ++claim) {
+        uint32_t c = *reinterpret_cast<volatile uint32_t*>(pf_counter);
+        if (c >= n_slices || (uint64_t)c * kPfSlice >= limit) break;
+        if (atomicCAS(pf_counter, c, c + 1) != c) continue;
+        const uint64_t o = (uint64_t)c * kPfSlice;
+        const uint64_t len = ((src_bytes - o) < kPfSlice ? (src_bytes - o) : kPfSlice) & ~uint64_t(15);
+        if (len) bulk_prefetch_l2(src + o, (uint32_t)len);
+      }
+    }
+    T v[kGatherUnroll];
+    bool ok[kGatherUnroll];
+#pragma unroll
+    for (int k = 0; k < kGatherUnroll; ++k) {
+      const uint64_t t = base + (uint64_t)k * kGatherThreads;
+      ok[k] = t < total;
+      if (ok[k]) {
+        const uint64_t i = fdiv(t, fdW);
+        const uint32_t w = (uint32_t)(t - i * W);
+        v[k] = s[(uint64_t)__ldg(run_rid + i) * W + w];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kGatherUnroll; ++k)
+      if (ok[k]) st_stream(d + base + (uint64_t)k * kGatherThreads, v[k]);
+  }
+}
+
 // Sets the range bit when n > 0 rids address an empty source table.
 __global__ void k_flag_range(int* err) { atomicOr(err, ERR_RANGE); }
 
@@ -526,6 +675,8 @@ void launch_probe(dpg_ctx& ctx, uint32_t WB, const Retrieval& r, uint32_t seg_lo
 #undef DPG_PROBE
   ctx.launches++;
 }
+
+int run_dpg_l2(dpg_ctx& ctx, const Retrieval& r, const Plan& plan);
 
 template <class Rid, typename LoT>
 int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
@@ -621,6 +772,106 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   return DPG_OK;
 }
 
+
+// Variant 4 (L2 runs): k_hist -> k_bucket_totals -> k_scan -> k_partition ->
+// k_probe_l2 -> k_gather_phase3.
+template <class Rid>
+int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
+  const uint32_t sl = (uint32_t)plan.seg_log2;
+  const uint64_t S = 1ull << sl;
+  const uint32_t nb = (uint32_t)((r.n_src + S - 1) >> sl);
+  if (nb > kPartMaxRuns) return DPG_EINVAL;
+  const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)ctx.sms * 2, (r.n + 8191) / 8192));
+  const uint32_t G = grid;
+  const uint64_t per = (r.n + grid - 1) / grid;
+  const uint32_t chunk = 1u << 30;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const bool strided = !std::is_same<Rid, RidArray>::value;
+  const size_t b_cnt = al((size_t)nb * G * 4), b_tot = al((size_t)nb * 4), b_off = al(((size_t)nb + 1) * 4);
+  const size_t b_ctr = 256, b_ts = al((size_t)((nb + kScanTile - 1) / kScanTile) * 4);
+  const size_t b_run = al(r.n * 4), b_slot = al(r.n * 4), b_rc = strided ? al(r.n * 4) : 0;
+  const size_t b_stage = al(r.n * r.rec);
+  const size_t need = b_cnt + b_tot + 2 * b_off + 2 * b_ctr + 2 * b_ts + b_run + b_slot + b_rc + b_stage;
+  if (int s = ensure_scratch(ctx, need)) return s;
+  uint8_t* p = static_cast<uint8_t*>(ctx.scratch);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(p); p += b_cnt;
+  uint32_t* tot = reinterpret_cast<uint32_t*>(p); p += b_tot;
+  uint32_t* off = reinterpret_cast<uint32_t*>(p); p += b_off;
+  uint32_t* itemoff = reinterpret_cast<uint32_t*>(p); p += b_off;
+  uint32_t* counter = reinterpret_cast<uint32_t*>(p); p += b_ctr;
+  uint32_t* pf = reinterpret_cast<uint32_t*>(p); p += b_ctr;
+  uint32_t* tsum = reinterpret_cast<uint32_t*>(p); p += b_ts;
+  uint32_t* isum = reinterpret_cast<uint32_t*>(p); p += b_ts;
+  uint32_t* run_rid = reinterpret_cast<uint32_t*>(p); p += b_run;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(p); p += b_slot;
+  int32_t* rc = strided ? reinterpret_cast<int32_t*>(p) : nullptr; p += b_rc;
+  uint8_t* stage = p;
+
+  cudaError_t e = cudaMemsetAsync(tsum, 0, 2 * b_ts, r.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pf, 0, 4, r.stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  const size_t phase_smem = (size_t)nb * 4;
+  {
+    TraceScope ts(ctx, "k_hist", r.stream);
+    auto kern = k_hist<Rid>;
+    set_smem(kern, phase_smem);
+    kern<<<grid, kPhaseThreads, phase_smem, r.stream>>>(rid, r.n, (uint32_t)r.n_src, sl, nb, G, per, cnt, tot,
+                                                        ctx.d_err, 1, rc);
+  }
+  {
+    TraceScope ts(ctx, "k_bucket_totals", r.stream);
+    k_bucket_totals<<<(nb + 31) / 32, 1024, 0, r.stream>>>(cnt, tot, nb, G, chunk, tsum, isum, ctx.d_err, 1);
+  }
+  {
+    TraceScope ts(ctx, "k_scan", r.stream);
+    k_scan<<<(nb + 31) / 32, 1024, 0, r.stream>>>(tot, tsum, isum, nb, G, chunk, cnt, off, itemoff, counter,
+                                                  ctx.d_err);
+  }
+  {
+    TraceScope ts(ctx, "k_partition", r.stream);
+    const RidArray ra{strided ? rc : reinterpret_cast<const int32_t*>(r.rids.base)};
+    k_partition<RidArray><<<grid, kPhaseThreads, 0, r.stream>>>(ra, r.n, sl, nb, G, per, cnt, run_rid, slot,
+                                                                ctx.d_err);
+  }
+  {
+    TraceScope ts(ctx, "k_probe_l2", r.stream);
+    const uintptr_t sa = reinterpret_cast<uintptr_t>(r.src);
+    const uint32_t wb = std::min(pow2_align(r.rec), pow2_align(sa));
+    const uint32_t W = r.rec / wb;
+    const FastDiv f = make_fastdiv(W);
+    const uint64_t total = r.n * W;
+    const uint64_t per_block = (uint64_t)kGatherThreads * kGatherUnroll;
+    // keep the records in flight (one grid step) within about DPG_L2_WINDOW_KB
+    // kilobytes (default 4 MB) so the run being probed stays L2-resident
+    const uint64_t window = (uint64_t)env_int("DPG_L2_WINDOW_KB", 4096) << 10;
+    const uint64_t by_window = std::max<uint64_t>(1, window / (per_block * wb));
+    const int pgrid = (int)std::max<uint64_t>(1, std::min<uint64_t>({(total + per_block - 1) / per_block,
+                                                                     (uint64_t)ctx.sms * 8,
+                                                                     std::max<uint64_t>(by_window, ctx.sms)}));
+    const int use_pf = (sa % 16 == 0) ? 1 : 0;
+    const uint64_t rb = S * r.rec, sb = r.n_src * r.rec;
+    switch (wb) {
+      case 16: k_probe_l2<16><<<pgrid, kGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, off, nb, rb, sb, pf, use_pf, ctx.d_err); break;
+      case 8: k_probe_l2<8><<<pgrid, kGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, off, nb, rb, sb, pf, use_pf, ctx.d_err); break;
+      case 4: k_probe_l2<4><<<pgrid, kGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, off, nb, rb, sb, pf, use_pf, ctx.d_err); break;
+      case 2: k_probe_l2<2><<<pgrid, kGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, off, nb, rb, sb, pf, use_pf, ctx.d_err); break;
+      default: k_probe_l2<1><<<pgrid, kGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, off, nb, rb, sb, pf, use_pf, ctx.d_err); break;
+    }
+  }
+  ctx.launches += 5;
+  const uint32_t wb = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
+  launch_gather<SlotArray, false>(ctx, wb, stage, r.dst, SlotArray{slot}, r.n, r.rec, (uint32_t)r.n_src, r.stream);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "dpg l2 launch");
+  return DPG_OK;
+}
+
+int run_dpg_l2(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {
+  if (r.rids.stride == 4)
+    return run_dpg_l2_t<RidArray>(ctx, r, RidArray{reinterpret_cast<const int32_t*>(r.rids.base)}, plan);
+  return run_dpg_l2_t<RidStrided>(ctx, r, RidStrided{r.rids.base, r.rids.stride}, plan);
+}
+
 }  // namespace
 
 Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
@@ -634,6 +885,15 @@ Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
   const int o = env_int("DPG_SEG_LOG2", -1);
   if (o >= 0 && (1ull << o) * r.rec <= kSegBytesMax) p.seg_log2 = o;
   p.chunk = (uint32_t)env_int("DPG_CHUNK", 0);
+  if (p.variant == 4) {
+    // runs of about DPG_L2_RUN_KB kilobytes of source (default 16 MB), at
+    // most kPartMaxRuns of them
+    const uint64_t want = (uint64_t)env_int("DPG_L2_RUN_KB", 16384) << 10;
+    int k = 0;
+    while (k < 31 && ((2ull << k) * r.rec) <= want) ++k;
+    while (k < 31 && ((r.n_src + (1ull << k) - 1) >> k) > kPartMaxRuns) ++k;
+    p.seg_log2 = k;
+  }
   return p;
 }
 
@@ -645,6 +905,7 @@ int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "flag");
   }
+  if (plan.variant == 4) return run_dpg_l2(ctx, r, plan);
   if ((1ull << plan.seg_log2) * r.rec > kSegBytesMax && plan.seg_log2 > 0) return DPG_EINVAL;
   const bool lo16 = plan.seg_log2 <= 16;
   if (r.rids.stride == 4) {

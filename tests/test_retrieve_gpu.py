@@ -60,11 +60,12 @@ def check(ctx, src, rids, variants=("dpg", "direct")):
 RECS = [1, 2, 3, 4, 7, 8, 12, 16, 17, 32, 64, 100, 128, 255, 256, 1000, 4096]
 
 
-@pytest.mark.parametrize("variant", ["3", "2"])
+@pytest.mark.parametrize("variant", ["3", "2", "4"])
 @pytest.mark.parametrize("kind", ["perm", "dup", "skew"])
 @pytest.mark.parametrize("rec", RECS)
 def test_retrieve_matches_oracle(ctx, monkeypatch, rec, kind, variant):
     monkeypatch.setenv("DPG_VARIANT", variant)
+    monkeypatch.setenv("DPG_L2_RUN_KB", "256")   # several L2 runs at these sizes
     n_src = max(37, min(60000, (3 << 20) // rec)) | 1       # several segments and a ragged tail
     n = n_src + 333 if kind != "perm" else n_src
     src = synth.records(n_src, rec, rec)
@@ -85,8 +86,21 @@ def test_forced_small_segments(ctx, monkeypatch, seg_log2, chunk, variant):
         check(ctx, src, rid_sequence(kind, n_src, 70001 if kind != "perm" else n_src, 9), variants=("dpg",))
 
 
+@pytest.mark.parametrize("run_kb", ["1", "64", "100000"])
+def test_l2_runs(ctx, monkeypatch, run_kb):
+    """L2-run plan: one run, a few runs, and the run-count cap (1024 runs)."""
+    monkeypatch.setenv("DPG_VARIANT", "4")
+    monkeypatch.setenv("DPG_L2_RUN_KB", run_kb)
+    for n_src, rec in ((200_003, 16), (50_001, 100), (3001, 1000)):
+        src = synth.records(n_src, rec, 11)
+        for kind in ("perm", "dup", "same"):
+            check(ctx, src, rid_sequence(kind, n_src, 120_001 if kind != "perm" else n_src, 4), variants=("dpg",))
+
+
+@pytest.mark.parametrize("variant", ["3", "4"])
 @pytest.mark.parametrize("n_src,n", [(1, 1), (1, 1000), (2, 1), (5, 3), (1000, 1), (70000, 2)])
-def test_small_and_degenerate(ctx, n_src, n):
+def test_small_and_degenerate(ctx, monkeypatch, n_src, n, variant):
+    monkeypatch.setenv("DPG_VARIANT", variant)
     for rec in (1, 4, 100):
         src = synth.records(n_src, rec, n_src)
         check(ctx, src, synth.uniform_ids(n, n_src, n))
@@ -103,8 +117,11 @@ def test_empty(ctx):
     ctx.sync()
 
 
+@pytest.mark.parametrize("variant", ["3", "4"])
 @pytest.mark.parametrize("src_off,dst_off", [(1, 0), (0, 3), (4, 8), (8, 4), (2, 6), (16, 1)])
-def test_unaligned_tables(ctx, src_off, dst_off):
+def test_unaligned_tables(ctx, monkeypatch, src_off, dst_off, variant):
+    monkeypatch.setenv("DPG_VARIANT", variant)
+    monkeypatch.setenv("DPG_L2_RUN_KB", "64")
     n_src, n = 9001, 12000
     for rec in (16, 100, 64):
         src = synth.records(n_src, rec, 5)
@@ -124,9 +141,11 @@ def test_unaligned_tables(ctx, src_off, dst_off):
         assert int(bigd[:dst_off].sum()) == 0 and int(bigd[dst_off + n * rec:].sum()) == 0
 
 
+@pytest.mark.parametrize("variant", ["3", "2", "4"])
 @pytest.mark.parametrize("bad", [-1, 5000, 2**31 - 1])
-def test_bad_rid_leaves_destination_untouched(ctx, bad):
+def test_bad_rid_leaves_destination_untouched(ctx, monkeypatch, bad, variant):
     from paper_cs_0308004_gb300 import dpg
+    monkeypatch.setenv("DPG_VARIANT", variant)
     n_src, rec = 5000, 100
     src = to_dev(synth.records(n_src, rec, 1))
     rids = synth.uniform_ids(20000, n_src, 2)
@@ -163,8 +182,10 @@ def test_argument_errors(ctx):
         ctx.retrieve(torch.zeros((2, 70000), dtype=torch.uint8, device=DEV), rids[:1].clone())
 
 
-def test_config1_full_size(ctx):
+@pytest.mark.parametrize("variant", ["3", "4"])
+def test_config1_full_size(ctx, monkeypatch, variant):
     """1,000,000 records of 100 bytes, a random permutation: full comparison."""
+    monkeypatch.setenv("DPG_VARIANT", variant)
     src, rids = synth.plain_retrieval(1_000_000, 100, 1, 2)
     check(ctx, src, rids)
     check(ctx, src, synth.uniform_ids(1_000_000, 1_000_000, 5))
@@ -172,8 +193,11 @@ def test_config1_full_size(ctx):
 
 # ------------------------------------------------------------ sort copy (§3)
 
+@pytest.mark.parametrize("variant", ["3", "4"])
 @pytest.mark.parametrize("rec", [16, 32, 64, 100, 256])
-def test_sort_copy_matches_oracle(ctx, rec):
+def test_sort_copy_matches_oracle(ctx, monkeypatch, rec, variant):
+    monkeypatch.setenv("DPG_VARIANT", variant)
+    monkeypatch.setenv("DPG_L2_RUN_KB", "1024")
     n = 200_003
     src = synth.sort_file(n, rec, 3)
     pairs = oracle.sort_keyptr(src, 10)
@@ -199,10 +223,12 @@ def test_sort_copy_other_pair_layouts(ctx):
             assert np.array_equal(out.cpu().numpy(), want)
 
 
-def test_sort_copy_full_size_sampled(ctx):
+@pytest.mark.parametrize("variant", ["3", "4"])
+def test_sort_copy_full_size_sampled(ctx, monkeypatch, variant):
     """10,000,000 records of 100 bytes (1 GB), pairs sorted by the oracle:
     sampled outputs against the oracle, plus the sortedness and permutation
     properties on the whole output."""
+    monkeypatch.setenv("DPG_VARIANT", variant)
     n, rec = 10_000_000, 100
     src = synth.sort_file(n, rec, 3)
     pairs = oracle.sort_keyptr(src, 10)

@@ -327,8 +327,20 @@ def main():
         ms = max_over_ranks(e0.elapsed_time(e1))
         return ms / a.steps, ctx.kernel_launches - l0, (t_wall0, t_wall1)
 
+    # the GPU key-pointer sort (§3 phases 1-2) must reproduce the pairs prepared on the host
+    g_pairs = ctx.sort_keyptr(d_src, 10)
+    ctx.sync()
+    assert torch.equal(g_pairs, d_pairs), "GPU key-pointer sort differs from the host-prepared pairs"
+    del g_pairs
+
     ms_dpg, launches, win = timed(lambda: ctx.sort_copy(d_pairs, d_src, out=d_out))
     ms_dir, launches_dir, win_dir = timed(lambda: ctx.sort_copy_direct(d_pairs, d_src, out=d_out))
+
+    # the whole §3 sort (extract + radix sort + DPG copy) and its phases 1-2 alone
+    g_pairs = torch.empty_like(d_pairs)
+    ms_keyptr, _, _ = timed(lambda: ctx.sort_keyptr(d_src, 10, out=g_pairs))
+    ms_sortall, _, _ = timed(lambda: ctx.sort_records(d_src, 10, out=d_out))
+    del g_pairs
 
     # per-kernel CUDA-event durations on the launching stream
     ctx.trace_reset()
@@ -399,6 +411,9 @@ def main():
             "direct_gather": {"value": round(direct, 3), "unit": "GB/s", "ms_per_step": round(ms_dir, 4),
                               "pct_of_hbm_peak": round(direct / world / peak, 4)},
             "speedup_vs_direct": round(ms_dir / ms_dpg, 4),
+            "full_sort": {"ms_per_sort": round(ms_sortall, 4), "keyptr_sort_ms": round(ms_keyptr, 4),
+                          "records_per_s": round(world * n / (ms_sortall * 1e-3), 1),
+                          "what": "dpg_sort_records: extract pairs + stable 10-pass LSD radix sort + DPG copy"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": None},

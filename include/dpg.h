@@ -104,6 +104,22 @@ dpg_status dpg_sort_copy_direct(dpg_ctx* ctx, const void* pairs, size_t pair_str
                                 size_t rid_off, size_t n, const void* src, size_t n_src,
                                 size_t rec_bytes, void* dst, void* stream);
 
+/*
+ * Phases 1 and 2 of the three-phase sort (§3): the key-pointer pair of every
+ * record (its first key_bytes bytes, 1 <= key_bytes <= 12, as the key), sorted
+ * by key as unsigned byte strings, equal keys in rid order.  `pairs` receives
+ * n_src pairs of 16 bytes: key bytes, zero padding to byte 12, int32 rid at
+ * byte 12 (the layout dpg_sort_copy reads with pair_stride 16, rid_off 12).
+ * Stable LSD radix sort, one key byte per pass.
+ */
+dpg_status dpg_sort_keyptr(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes, size_t key_bytes,
+                           void* pairs, void* stream);
+
+/* The whole §3 sort: dst[i] = the record of rank i in (key, rid) order, i.e.
+ * dpg_sort_keyptr followed by dpg_sort_copy (DPG record retrieval). */
+dpg_status dpg_sort_records(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes, size_t key_bytes,
+                            void* dst, void* stream);
+
 /* Blocks until `stream` has finished, then returns the first asynchronous
  * error raised by this context's kernels since the previous dpg_sync
  * (DPG_ERANGE, DPG_ETIMEOUT) and clears it; DPG_OK when there was none. */

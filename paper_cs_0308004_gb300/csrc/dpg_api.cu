@@ -115,6 +115,27 @@ int ensure_scratch(dpg_ctx& ctx, size_t bytes) {
   return DPG_OK;
 }
 
+int ensure_aux(dpg_ctx& ctx, size_t bytes) {
+  if (bytes <= ctx.aux_bytes) return DPG_OK;
+  const size_t grain = size_t(2) << 20;
+  const size_t want = (bytes + grain - 1) / grain * grain;
+  if (ctx.aux) {
+    cudaError_t e = cudaFree(ctx.aux);
+    ctx.aux = nullptr;
+    ctx.aux_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFree(aux)");
+  }
+  cudaError_t e = cudaMalloc(&ctx.aux, want);
+  if (e != cudaSuccess) {
+    ctx.aux = nullptr;
+    cudaGetLastError();
+    ctx.last_error = std::string("cudaMalloc(aux): ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? DPG_ENOMEM : DPG_ECUDA;
+  }
+  ctx.aux_bytes = want;
+  return DPG_OK;
+}
+
 }  // namespace dpg
 
 extern "C" {
@@ -171,6 +192,7 @@ void dpg_ctx_destroy(dpg_ctx* c) {
     }
     for (cudaEvent_t e : c->trace_pool) cudaEventDestroy(e);
     if (c->io) cudaFree(c->io);
+    if (c->aux) cudaFree(c->aux);
     if (c->scratch) cudaFree(c->scratch);
     if (c->d_err) cudaFree(c->d_err);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -251,6 +273,49 @@ dpg_status dpg_sync(dpg_ctx* c, void* stream) {
   return DPG_OK;
 }
 
+// ---- §3 sort: key-pointer pairs and the whole three-phase sort.
+
+static int check_sort(dpg_ctx* c, const void* src, size_t n_src, size_t rec, size_t key_bytes, const void* out) {
+  if (!c || rec == 0 || key_bytes == 0 || key_bytes > 12 || key_bytes > rec) return DPG_EINVAL;
+  if (n_src > 0x7fffffffULL || rec > (1ull << 30)) return DPG_EINVAL;
+  if (n_src && (!src || !out)) return DPG_EINVAL;
+  return DPG_OK;
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+dpg_status dpg_sort_keyptr(dpg_ctx* c, const void* src, size_t n_src, size_t rec, size_t key_bytes, void* pairs,
+                           void* stream) {
+  int s = check_sort(c, src, n_src, rec, key_bytes, pairs);
+  if (s != DPG_OK || n_src == 0) return (dpg_status)s;
+  if (overlaps(src, n_src * rec, pairs, n_src * 16)) return DPG_EINVAL;
+  DeviceGuard g(c->device);
+  const size_t bt = al256(n_src * 16), bs = dpg::sort_scan_bytes(n_src);
+  if ((s = dpg::ensure_aux(*c, bt + bs))) return (dpg_status)s;
+  uint8_t* tmp = static_cast<uint8_t*>(c->aux);
+  return (dpg_status)dpg::run_sort_keyptr(*c, static_cast<const uint8_t*>(src), n_src, (uint32_t)rec,
+                                          (uint32_t)key_bytes, static_cast<uint8_t*>(pairs), tmp, tmp + bt,
+                                          static_cast<cudaStream_t>(stream));
+}
+
+dpg_status dpg_sort_records(dpg_ctx* c, const void* src, size_t n_src, size_t rec, size_t key_bytes, void* dst,
+                            void* stream) {
+  int s = check_sort(c, src, n_src, rec, key_bytes, dst);
+  if (s != DPG_OK || n_src == 0) return (dpg_status)s;
+  if (rec > dpg::kMaxDpgRecBytes || overlaps(src, n_src * rec, dst, n_src * rec)) return DPG_EINVAL;
+  DeviceGuard g(c->device);
+  const size_t bp = al256(n_src * 16), bs = dpg::sort_scan_bytes(n_src);
+  if ((s = dpg::ensure_aux(*c, 2 * bp + bs))) return (dpg_status)s;
+  uint8_t* pairs = static_cast<uint8_t*>(c->aux);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = dpg::run_sort_keyptr(*c, static_cast<const uint8_t*>(src), n_src, (uint32_t)rec, (uint32_t)key_bytes, pairs,
+                           pairs + bp, pairs + 2 * bp, st);
+  if (s != DPG_OK) return (dpg_status)s;
+  dpg::Retrieval r{static_cast<const uint8_t*>(src), n_src, (uint32_t)rec, n_src,
+                   dpg::RidSpec{pairs + 12, 16}, static_cast<uint8_t*>(dst), st};
+  return (dpg_status)dpg::run_dpg(*c, r, dpg::choose_plan(*c, r));
+}
+
 void dpg_trace_enable(dpg_ctx* c, int on) {
   if (!c) return;
   DeviceGuard g(c->device);
@@ -305,8 +370,6 @@ static int ensure_io(dpg_ctx& c, size_t bytes) {
   c.io_bytes = want;
   return DPG_OK;
 }
-
-static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 dpg_status dpg_retrieve_host(dpg_ctx* c, const void* src, size_t n_src, size_t rec, size_t n,
                              const int32_t* rids, void* dst, void* stream) {

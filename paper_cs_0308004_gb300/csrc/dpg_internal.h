@@ -25,6 +25,10 @@ struct dpg_ctx {
   // host-buffer entry points: device copies of the caller's tables
   void* io = nullptr;
   size_t io_bytes = 0;
+  // sort and join work space (kept apart from the retrieval scratch, which a
+  // sort or join hands to a retrieval while its own buffers are live)
+  void* aux = nullptr;
+  size_t aux_bytes = 0;
   // kernel tracing: CUDA events recorded around every launch on its stream
   bool trace = false;
   struct TraceRec {
@@ -81,6 +85,12 @@ int run_direct(dpg_ctx& ctx, const Retrieval& r);
 
 // Scratch arena helpers (dpg_api.cu).
 int ensure_scratch(dpg_ctx& ctx, size_t bytes);
+int ensure_aux(dpg_ctx& ctx, size_t bytes);
+
+// Phases 1-2 of the §3 sort (dpg_sort.cu): sorted 16-byte key-pointer pairs.
+size_t sort_scan_bytes(uint64_t n);
+int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, uint32_t key_bytes, uint8_t* pairs,
+                    uint8_t* tmp, uint8_t* scan, cudaStream_t st);
 int cuda_fail(dpg_ctx& ctx, cudaError_t e, const char* what);
 
 // Brackets one kernel launch with CUDA events on its stream when tracing is on.

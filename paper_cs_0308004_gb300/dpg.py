@@ -43,6 +43,8 @@ SIGNATURES = {
     "dpg_trace_get": ([_P, _S, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                        ctypes.POINTER(ctypes.c_uint64)], _I),
     "dpg_retrieve_noalloc": ([_P, _S, _S, _S, _P, _P, _P], _I),
+    "dpg_sort_keyptr": ([_P, _P, _S, _S, _S, _P, _P], _I),
+    "dpg_sort_records": ([_P, _P, _S, _S, _S, _P, _P], _I),
 }
 
 
@@ -186,6 +188,34 @@ class Context:
 
     def sort_copy_direct(self, pairs, src, rid_off: int = PAIR_RID_OFF, out=None, stream=None):
         return self._sort_copy(lib.dpg_sort_copy_direct, pairs, src, rid_off, out, stream)
+
+    def sort_keyptr(self, src: torch.Tensor, key_bytes: int = 10, out: torch.Tensor | None = None, stream=None):
+        """§3 phases 1-2: sorted (n_src, 16) uint8 key-pointer pairs of src."""
+        _need_cuda(src, "src", self.device)
+        n_src, rec = _table(src, "src")
+        if out is None:
+            out = torch.empty((n_src, PAIR_BYTES), dtype=torch.uint8, device=self.device)
+        _need_cuda(out, "out", self.device)
+        if tuple(out.shape) != (n_src, PAIR_BYTES) or out.dtype != torch.uint8:
+            raise ValueError("out must be a uint8 tensor of shape (records, 16)")
+        st = lib.dpg_sort_keyptr(self._h, src.data_ptr(), n_src, rec, key_bytes, out.data_ptr(),
+                                 _stream_handle(stream, self.device))
+        self._check(st, "dpg_sort_keyptr")
+        return out
+
+    def sort_records(self, src: torch.Tensor, key_bytes: int = 10, out: torch.Tensor | None = None, stream=None):
+        """The whole §3 sort: records in (key, rid) order."""
+        _need_cuda(src, "src", self.device)
+        n_src, rec = _table(src, "src")
+        if out is None:
+            out = torch.empty((n_src, rec), dtype=torch.uint8, device=self.device)
+        _need_cuda(out, "out", self.device)
+        if tuple(out.shape) != (n_src, rec) or out.dtype != torch.uint8:
+            raise ValueError("out must be a uint8 tensor shaped like src")
+        st = lib.dpg_sort_records(self._h, src.data_ptr(), n_src, rec, key_bytes, out.data_ptr(),
+                                  _stream_handle(stream, self.device))
+        self._check(st, "dpg_sort_records")
+        return out
 
     # -- host buffers (copies in and out happen inside the library)
     @staticmethod

@@ -1,0 +1,92 @@
+"""Parity of the GPU three-phase sort (§3) with the oracle, byte for byte:
+key-pointer pairs (dpg_sort_keyptr) and sorted records (dpg_sort_records),
+over ragged tile counts, record sizes, key lengths, ties, and the full-size
+10,000,000 x 100-byte file."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_cs_0308004_gb300 import dpg
+    c = dpg.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def tie_heavy(n, rec, seed):
+    src = synth.records(n, rec, seed).copy()
+    src[::3, :10] = src[0, :10]             # a third of the keys equal
+    if n > 1:
+        src[1::7, :9] = src[1, :9]          # keys equal but for the last key byte
+    src[2::11, 0] = 0xff                    # top byte saturated
+    return src
+
+
+@pytest.mark.parametrize("n", [1, 2, 100, 4095, 4096, 4097, 100_003])
+@pytest.mark.parametrize("rec,key_bytes", [(10, 10), (16, 10), (100, 10), (13, 3), (12, 12), (256, 1), (100, 7)])
+def test_sort_keyptr_matches_oracle(ctx, n, rec, key_bytes):
+    for src in (synth.records(n, rec, n + rec), tie_heavy(n, rec, 5)):
+        want = oracle.sort_keyptr(src, key_bytes)
+        got = ctx.sort_keyptr(to_dev(src), key_bytes)
+        ctx.sync()
+        assert np.array_equal(got.cpu().numpy(), want)
+
+
+def test_sort_all_equal_keys(ctx):
+    n, rec = 50_001, 16
+    src = synth.records(n, rec, 9).copy()
+    src[:, :10] = 0x42
+    got = ctx.sort_keyptr(to_dev(src), 10)
+    ctx.sync()
+    assert np.array_equal(got.cpu().numpy(), oracle.sort_keyptr(src, 10))
+
+
+@pytest.mark.parametrize("variant", ["3", "4"])
+@pytest.mark.parametrize("rec", [16, 100, 256])
+def test_sort_records_matches_oracle(ctx, monkeypatch, rec, variant):
+    monkeypatch.setenv("DPG_VARIANT", variant)
+    n = 300_007
+    src = tie_heavy(n, rec, rec)
+    got = ctx.sort_records(to_dev(src), 10)
+    ctx.sync()
+    assert np.array_equal(got.cpu().numpy(), oracle.sort_records(src, 10))
+
+
+def test_sort_full_size(ctx):
+    """10,000,000 records of 100 bytes: every pair against the oracle, the
+    sorted file sampled against the oracle's sort copy."""
+    n, rec = 10_000_000, 100
+    src = synth.sort_file(n, rec, 3)
+    want_pairs = oracle.sort_keyptr(src, 10)
+    d_src = to_dev(src)
+    got = ctx.sort_keyptr(d_src, 10)
+    ctx.sync()
+    assert torch.equal(got, to_dev(want_pairs))
+    out = ctx.sort_records(d_src, 10)
+    ctx.sync()
+    idx = np.sort(synth.uniform_ids(50_000, n, 3)).astype(np.int64)
+    want = oracle.retrieve(src, oracle.pair_rids(want_pairs)[idx])
+    assert np.array_equal(out[torch.from_numpy(idx).to(DEV)].cpu().numpy(), want)
+
+
+def test_sort_argument_errors(ctx):
+    from paper_cs_0308004_gb300 import dpg
+    src = to_dev(synth.records(100, 8, 1))
+    for kb in (0, 13, 9):
+        with pytest.raises(dpg.DpgError):
+            ctx.sort_keyptr(src, kb)
+    empty = torch.zeros((0, 8), dtype=torch.uint8, device=DEV)
+    assert ctx.sort_keyptr(empty, 4).shape == (0, 16)

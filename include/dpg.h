@@ -120,6 +120,31 @@ dpg_status dpg_sort_keyptr(dpg_ctx* ctx, const void* src, size_t n_src, size_t r
 dpg_status dpg_sort_records(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes, size_t key_bytes,
                             void* dst, void* stream);
 
+/*
+ * Foreign-key join (§4.2): the fact relation has n_fact rows of fact_bytes
+ * bytes with an int32 foreign key at byte fk_off (fact_bytes, fk_off and the
+ * fact pointer multiples of 4); the dimension relation has n_dim rows of
+ * dim_bytes bytes whose int64 key at byte pk_off equals the row number (the
+ * dimension's index maps key k to row k).  `out` receives n_fact rows of
+ * fact_bytes + dim_bytes bytes, each a fact row followed by the dimension row
+ * its key names:
+ *   DPG_JOIN_MOVE   DPG-move join (§4.2.1): out[i] = fact[i] || dim[fk_i],
+ *                   the dimension rows moved into fact order by DPG.
+ *   DPG_JOIN_SORT   DPG-sort join (§4.2.1): the (fk, i) pairs sorted by fk
+ *                   (ties by fact row) and fact rows moved into that order by
+ *                   DPG: out[j] = fact[i_j] || dim[fk_j].
+ *   DPG_JOIN_DIRECT the MOVE result in one direct pass (baseline).
+ * A foreign key outside [0, n_dim), or a referenced dimension row whose key
+ * differs from its row number, is reported by dpg_sync as DPG_ERANGE.  MOVE
+ * and SORT catch an out-of-range key before writing `out`; MOVE also checks
+ * dimension keys before writing; SORT and DIRECT check dimension keys as they
+ * copy (then `out` is partly written).
+ */
+enum { DPG_JOIN_MOVE = 0, DPG_JOIN_SORT = 1, DPG_JOIN_DIRECT = 2 };
+dpg_status dpg_fk_join(dpg_ctx* ctx, const void* fact, size_t n_fact, size_t fact_bytes, size_t fk_off,
+                       const void* dim, size_t n_dim, size_t dim_bytes, size_t pk_off, void* out, int mode,
+                       void* stream);
+
 /* Blocks until `stream` has finished, then returns the first asynchronous
  * error raised by this context's kernels since the previous dpg_sync
  * (DPG_ERANGE, DPG_ETIMEOUT) and clears it; DPG_OK when there was none. */

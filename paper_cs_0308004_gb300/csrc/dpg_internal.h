@@ -61,6 +61,29 @@ struct RidSpec {
   uint32_t stride;       // bytes between consecutive rids (4 for a plain array)
 };
 
+// A foreign-key join riding on a retrieval (§4.2.1): Phase III writes join
+// rows instead of plain records.
+//   mode 0 (DPG-move): the retrieval moves dimension rows into fact order;
+//          out row i = fact[i] || INTERNAL[slot[i]].  Phase II checks that
+//          each probed dimension row's key equals its row number.
+//   mode 1 (DPG-sort): the retrieval moves fact rows into the order of the
+//          (fk, fact row) pairs sorted by fk; out row j = INTERNAL[slot[j]] ||
+//          dim[fk_j], fk_j decoded from sorted pair j (key bytes [0, key_bytes)
+//          hold fk big-endian), the key of dim[fk_j] checked as it is copied.
+struct JoinSpec {
+  int mode;
+  const uint8_t* fact;
+  uint32_t fact_bytes;
+  uint32_t fk_off;
+  const uint8_t* dim;
+  uint32_t dim_bytes;
+  uint32_t pk_off;
+  uint64_t n_dim;
+  uint8_t* out;
+  const uint8_t* sorted_pairs;
+  uint32_t key_bytes;
+};
+
 struct Retrieval {
   const uint8_t* src;
   uint64_t n_src;
@@ -69,6 +92,7 @@ struct Retrieval {
   RidSpec rids;
   uint8_t* dst;
   cudaStream_t stream;
+  const JoinSpec* join = nullptr;
 };
 
 // Limits of the DPG path.
@@ -86,6 +110,16 @@ int run_direct(dpg_ctx& ctx, const Retrieval& r);
 // Scratch arena helpers (dpg_api.cu).
 int ensure_scratch(dpg_ctx& ctx, size_t bytes);
 int ensure_aux(dpg_ctx& ctx, size_t bytes);
+
+// Foreign-key join output without DPG: out row i = fact[i] || dim[fk_i]
+// (dpg_retrieve.cu), the baseline of the join modes.
+int run_join_direct(dpg_ctx& ctx, const JoinSpec& j, uint64_t n_fact, cudaStream_t st);
+
+// Stable LSD radix sort of 16-byte pairs on key bytes [0, key_bytes) (dpg_sort.cu).
+// `a` holds the pairs; the result ends in `a` (even key_bytes) or `b`; the
+// returned pointer says which.
+uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
+                         cudaStream_t st, int* status);
 
 // Phases 1-2 of the §3 sort (dpg_sort.cu): sorted 16-byte key-pointer pairs.
 size_t sort_scan_bytes(uint64_t n);

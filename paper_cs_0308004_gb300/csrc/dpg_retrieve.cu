@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <type_traits>
 
@@ -194,12 +195,12 @@ __device__ __forceinline__ typename WordT<WB>::T probe_word(const typename WordT
   return sw[(uint32_t)lo_s[q] * W + w];
 }
 
-template <int WB, typename LoT, bool SCATTER>
+template <int WB, typename LoT, bool SCATTER, bool PK = false>
 __global__ void __launch_bounds__(kProbeThreads)
     k_probe(const uint8_t* __restrict__ src, uint32_t n_src, uint32_t rec, uint32_t seg_log2,
             const uint32_t* __restrict__ off, const uint32_t* __restrict__ itemoff, uint32_t nb, uint32_t chunk,
             const LoT* __restrict__ lo, const uint32_t* __restrict__ dest, uint8_t* __restrict__ out, uint32_t W,
-            FastDiv fdW, int* err, uint32_t* item_counter, int use_bulk, uint32_t seg_smem) {
+            FastDiv fdW, int* err, uint32_t* item_counter, int use_bulk, uint32_t seg_smem, uint32_t pk_off = 0) {
   using T = typename WordT<WB>::T;
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar;
@@ -280,6 +281,20 @@ __global__ void __launch_bounds__(kProbeThreads)
         wait_bulk = false;
       }
       __syncthreads();
+      if constexpr (PK) {
+        // join (§4.2.1, DPG-move): the dimension row of run entry q must carry
+        // its own row number as its int64 little-endian key at pk_off
+        bool bad = false;
+        for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
+          const uint32_t l = lo_s[q];
+          const uint8_t* pr = seg + (uint64_t)l * rec + pk_off;
+          uint64_t v = 0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v |= (uint64_t)pr[j] << (8 * j);
+          if (v != (((uint64_t)b << seg_log2) + l)) bad = true;
+        }
+        if (bad) atomicOr(err, ERR_RANGE);
+      }
       const uint64_t total = (uint64_t)nq * W;
       if constexpr (SCATTER || WB >= 16 || WB <= 2) {
         for (uint64_t t = threadIdx.x; t < total; t += blockDim.x) {
@@ -475,6 +490,125 @@ __global__ void __launch_bounds__(kGatherThreads)
   }
 }
 
+// ------------------------------------------------------------- join rows
+// out row r = A-part || B-part: wa words of row ia(r) of table A, then wb
+// words of row ib(r) of table B, written as one coalesced word stream.
+// CHECK_B: ib(r) must be below nrows_b (else the range bit, row skipped).
+// pk_check: the int64 little-endian key at byte pk_off of the B row must equal
+// ib(r) (else the range bit).
+struct RowIdentity {
+  __device__ __forceinline__ uint64_t operator()(uint64_t r) const { return r; }
+};
+struct RowSlot {
+  const uint32_t* p;
+  __device__ __forceinline__ uint64_t operator()(uint64_t r) const { return __ldg(p + r); }
+};
+struct RowField {  // int32 field of strided rows (a foreign-key column)
+  const uint8_t* base;
+  uint32_t stride;
+  __device__ __forceinline__ uint64_t operator()(uint64_t r) const {
+    return (uint64_t)(uint32_t)__ldg(reinterpret_cast<const int32_t*>(base + r * stride));
+  }
+};
+struct RowPairKey {  // big-endian key bytes [0, kb) of sorted 16-byte pair r
+  const uint8_t* pairs;
+  uint32_t kb;
+  __device__ __forceinline__ uint64_t operator()(uint64_t r) const {
+    const uint8_t* p = pairs + r * 16;
+    uint64_t v = 0;
+    for (uint32_t j = 0; j < kb; ++j) v = (v << 8) | __ldg(p + j);
+    return v;
+  }
+};
+
+template <int WB>
+__device__ __forceinline__ bool pk_bytes_match(const typename WordT<WB>::T& v, uint32_t word, uint32_t pk_off,
+                                               uint64_t key) {
+  uint8_t b[WB];
+  memcpy(b, &v, WB);
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < WB; ++j) {
+    const uint32_t pos = word * WB + j;
+    if (pos >= pk_off && pos < pk_off + 8) ok &= b[j] == (uint8_t)(key >> (8 * (pos - pk_off)));
+  }
+  return ok;
+}
+
+template <int WB, class IA, class IB, bool CHECK_B>
+__global__ void __launch_bounds__(kGatherThreads)
+    k_join_rows(const uint8_t* __restrict__ ta, IA ia, uint32_t wa, const uint8_t* __restrict__ tb, IB ib,
+                uint32_t wb, uint64_t nrows_b, uint8_t* __restrict__ out, uint64_t n, FastDiv fd_row,
+                uint32_t pk_off, int pk_check, int* err) {
+  using T = typename WordT<WB>::T;
+  if (!CHECK_B && error_set(err)) return;
+  const T* a = reinterpret_cast<const T*>(ta);
+  const T* bt = reinterpret_cast<const T*>(tb);
+  T* o = reinterpret_cast<T*>(out);
+  const uint32_t row_w = wa + wb;
+  const uint64_t total = n * row_w;
+  const uint64_t step = (uint64_t)gridDim.x * kGatherThreads * kGatherUnroll;
+  const uint32_t pk_w0 = pk_off / WB, pk_w1 = (pk_off + 8 + WB - 1) / WB;
+  bool bad = false;
+  for (uint64_t base = (uint64_t)blockIdx.x * kGatherThreads * kGatherUnroll + threadIdx.x; base < total;
+       base += step) {
+    T v[kGatherUnroll];
+    bool ok[kGatherUnroll];
+#pragma unroll
+    for (int k = 0; k < kGatherUnroll; ++k) {
+      const uint64_t t = base + (uint64_t)k * kGatherThreads;
+      ok[k] = false;
+      if (t < total) {
+        const uint64_t r = fdiv(t, fd_row);
+        const uint32_t w = (uint32_t)(t - r * row_w);
+        if (w < wa) {
+          v[k] = a[ia(r) * wa + w];
+          ok[k] = true;
+        } else {
+          const uint64_t key = ib(r);
+          const uint32_t wbw = w - wa;
+          if (!CHECK_B || key < nrows_b) {
+            v[k] = bt[key * wb + wbw];
+            ok[k] = true;
+            if (pk_check && wbw >= pk_w0 && wbw < pk_w1 && !pk_bytes_match<WB>(v[k], wbw, pk_off, key)) bad = true;
+          } else {
+            bad = true;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kGatherUnroll; ++k)
+      if (ok[k]) o[base + (uint64_t)k * kGatherThreads] = v[k];
+  }
+  if (bad) atomicOr(err, ERR_RANGE);
+}
+
+template <class IA, class IB, bool CHECK_B>
+void launch_join_rows(dpg_ctx& ctx, const char* name, uint32_t WB, const uint8_t* ta, IA ia, uint32_t a_bytes,
+                      const uint8_t* tb, IB ib, uint32_t b_bytes, uint64_t nrows_b, uint8_t* out, uint64_t n,
+                      uint32_t pk_off, int pk_check, cudaStream_t st) {
+  const uint32_t wa = a_bytes / WB, wb = b_bytes / WB;
+  const FastDiv f = make_fastdiv(wa + wb);
+  const uint64_t total = n * (wa + wb);
+  const uint64_t per_block = (uint64_t)kGatherThreads * kGatherUnroll;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((total + per_block - 1) / per_block,
+                                                                  (uint64_t)ctx.sms * 8));
+  TraceScope ts(ctx, name, st);
+#define DPG_JOIN(WBV)                                                                                           \
+  k_join_rows<WBV, IA, IB, CHECK_B><<<grid, kGatherThreads, 0, st>>>(ta, ia, wa, tb, ib, wb, nrows_b, out, n, f, \
+                                                                     pk_off, pk_check, ctx.d_err)
+  switch (WB) {
+    case 16: DPG_JOIN(16); break;
+    case 8: DPG_JOIN(8); break;
+    case 4: DPG_JOIN(4); break;
+    case 2: DPG_JOIN(2); break;
+    default: DPG_JOIN(1); break;
+  }
+#undef DPG_JOIN
+  ctx.launches++;
+}
+
 // Sets the range bit when n > 0 rids address an empty source table.
 __global__ void k_flag_range(int* err) { atomicOr(err, ERR_RANGE); }
 
@@ -516,10 +650,10 @@ void launch_gather(dpg_ctx& ctx, uint32_t WB, const uint8_t* src, uint8_t* dst, 
   ctx.launches++;
 }
 
-template <typename LoT, bool SCATTER>
+template <typename LoT, bool SCATTER, bool PK = false>
 void launch_probe(dpg_ctx& ctx, uint32_t WB, const Retrieval& r, uint32_t seg_log2, const uint32_t* off,
                   const uint32_t* itemoff, uint32_t nb, uint32_t chunk, const LoT* lo, const uint32_t* dest,
-                  uint8_t* out, uint32_t* counter, int use_bulk, size_t seg_smem) {
+                  uint8_t* out, uint32_t* counter, int use_bulk, size_t seg_smem, uint32_t pk_off = 0) {
   const uint32_t W = r.rec / WB;
   const size_t smem = seg_smem + kProbeSub * sizeof(LoT) + (SCATTER ? kProbeSub * 4 : 0);
   const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024 + 256)));
@@ -528,11 +662,11 @@ void launch_probe(dpg_ctx& ctx, uint32_t WB, const Retrieval& r, uint32_t seg_lo
   TraceScope ts(ctx, SCATTER ? "k_probe_scatter" : "k_probe", r.stream);
 #define DPG_PROBE(WBV)                                                                                         \
   {                                                                                                            \
-    auto kern = k_probe<WBV, LoT, SCATTER>;                                                                    \
+    auto kern = k_probe<WBV, LoT, SCATTER, PK>;                                                                \
     set_smem(kern, smem);                                                                                      \
     kern<<<grid, kProbeThreads, smem, r.stream>>>(r.src, (uint32_t)r.n_src, r.rec, seg_log2, off, itemoff, nb, \
                                                  chunk, lo, dest, out, W, f, ctx.d_err, counter, use_bulk,     \
-                                                 (uint32_t)seg_smem);                                          \
+                                                 (uint32_t)seg_smem, pk_off);                                  \
   }
   switch (WB) {
     case 16: DPG_PROBE(16) break;
@@ -558,7 +692,7 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   const uint32_t G = smem_mode ? grid : 1;
   const uint64_t per = (r.n + grid - 1) / grid;
   const uint32_t chunk = plan.chunk ? plan.chunk : (uint32_t)std::min<uint64_t>(4 * S, 1u << 20);
-  const bool three = plan.variant != 2;
+  const bool three = plan.variant != 2 || r.join != nullptr;
 
   // scratch layout, each piece 256-byte aligned
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -624,13 +758,31 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   if (!three) wb_probe = std::min(wb_probe, pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
   if (!use_bulk) wb_probe = std::min(wb_probe, pow2_align(src_a));
   const size_t probe_smem = ((size_t)seg_bytes + 15) & ~size_t(15);
-  if (three)
+  if (r.join && r.join->mode == 0)
+    launch_probe<LoT, false, true>(ctx, wb_probe, r, sl, off, itemoff, nb, chunk, lo, nullptr, stage, counter,
+                                   use_bulk, probe_smem, r.join->pk_off);
+  else if (three)
     launch_probe<LoT, false>(ctx, wb_probe, r, sl, off, itemoff, nb, chunk, lo, nullptr, stage, counter, use_bulk,
                              probe_smem);
   else
     launch_probe<LoT, true>(ctx, wb_probe, r, sl, off, itemoff, nb, chunk, lo, side, r.dst, counter, use_bulk,
                             probe_smem);
-  if (three) {
+  if (r.join) {
+    // Phase III writing join rows
+    const JoinSpec& j = *r.join;
+    const uint32_t wb = std::min({pow2_align(j.fact_bytes), pow2_align(j.dim_bytes),
+                                  pow2_align(reinterpret_cast<uintptr_t>(j.out)),
+                                  pow2_align(reinterpret_cast<uintptr_t>(j.fact)),
+                                  pow2_align(reinterpret_cast<uintptr_t>(j.dim))});
+    if (j.mode == 0)
+      launch_join_rows<RowIdentity, RowSlot, false>(ctx, "k_join_move_rows", wb, j.fact, RowIdentity{}, j.fact_bytes,
+                                                    stage, RowSlot{side}, j.dim_bytes, j.n_dim, j.out, r.n,
+                                                    j.pk_off, 0, r.stream);
+    else
+      launch_join_rows<RowSlot, RowPairKey, false>(ctx, "k_join_sort_rows", wb, stage, RowSlot{side}, j.fact_bytes,
+                                                   j.dim, RowPairKey{j.sorted_pairs, j.key_bytes}, j.dim_bytes,
+                                                   j.n_dim, j.out, r.n, j.pk_off, 1, r.stream);
+  } else if (three) {
     // Phase III
     const uint32_t wb = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
     launch_gather<SlotArray, false>(ctx, wb, stage, r.dst, SlotArray{side}, r.n, r.rec, (uint32_t)r.n_src,
@@ -754,6 +906,7 @@ Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
   const int o = env_int("DPG_SEG_LOG2", -1);
   if (o >= 0 && (1ull << o) * r.rec <= kSegBytesMax) p.seg_log2 = o;
   p.chunk = (uint32_t)env_int("DPG_CHUNK", 0);
+  if (r.join) p.variant = 3;  // joins write join rows in the 3-pass Phase III
   if (p.variant == 4) {
     // runs of about DPG_L2_RUN_KB kilobytes of source (default 16 MB), at
     // most kPartMaxRuns of them
@@ -774,7 +927,7 @@ int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "flag");
   }
-  if (plan.variant == 4) return run_dpg_l2(ctx, r, plan);
+  if (plan.variant == 4 && !r.join) return run_dpg_l2(ctx, r, plan);
   if ((1ull << plan.seg_log2) * r.rec > kSegBytesMax && plan.seg_log2 > 0) return DPG_EINVAL;
   const bool lo16 = plan.seg_log2 <= 16;
   if (r.rids.stride == 4) {
@@ -783,6 +936,19 @@ int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {
   }
   RidStrided s{r.rids.base, r.rids.stride};
   return lo16 ? run_dpg_t<RidStrided, uint16_t>(ctx, r, s, plan) : run_dpg_t<RidStrided, uint32_t>(ctx, r, s, plan);
+}
+
+int run_join_direct(dpg_ctx& ctx, const JoinSpec& j, uint64_t n_fact, cudaStream_t st) {
+  if (n_fact == 0) return DPG_OK;
+  const uint32_t wb = std::min({pow2_align(j.fact_bytes), pow2_align(j.dim_bytes),
+                                pow2_align(reinterpret_cast<uintptr_t>(j.out)),
+                                pow2_align(reinterpret_cast<uintptr_t>(j.fact)),
+                                pow2_align(reinterpret_cast<uintptr_t>(j.dim))});
+  launch_join_rows<RowIdentity, RowField, true>(ctx, "k_join_direct_rows", wb, j.fact, RowIdentity{}, j.fact_bytes,
+                                                j.dim, RowField{j.fact + j.fk_off, j.fact_bytes}, j.dim_bytes,
+                                                j.n_dim, j.out, n_fact, j.pk_off, 1, st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "join direct launch");
 }
 
 int run_direct(dpg_ctx& ctx, const Retrieval& r) {
@@ -964,7 +1130,7 @@ extern "C" dpg_status dpg_retrieve_noalloc(const void* src_v, size_t n_src, size
       const uint32_t W = (uint32_t)rec / WBV;
       kp<<<sms * 2, kProbeThreads, smem, st>>>(src, (uint32_t)n_src, (uint32_t)rec, sl, off, itemoff, nb, chunk,
                                                 lo, dest, dst, W, make_fastdiv(W), err, counter, use_bulk,
-                                                (uint32_t)probe_smem);
+                                                (uint32_t)probe_smem, 0u);
     });
   }
   e = cudaGetLastError();

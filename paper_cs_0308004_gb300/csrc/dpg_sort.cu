@@ -159,35 +159,34 @@ size_t sort_scan_bytes(uint64_t n) {
   return ((256 * ntiles * 4 + 255) & ~255ull) + 4096;
 }
 
-int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, uint32_t key_bytes, uint8_t* pairs,
-                    uint8_t* tmp, uint8_t* scan, cudaStream_t st) {
-  if (n == 0) return DPG_OK;
+uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint64_t n, uint32_t key_bytes,
+                         cudaStream_t st, int* status) {
+  *status = DPG_OK;
+  uint4* a = reinterpret_cast<uint4*>(a_);
+  uint4* b = reinterpret_cast<uint4*>(b_);
+  if (n == 0) return a_;
   const uint32_t ntiles = (uint32_t)((n + kRsTile - 1) / kRsTile);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(scan);
   uint8_t* rest = scan + ((256ull * ntiles * 4 + 255) & ~255ull);
-  uint32_t* tot = reinterpret_cast<uint32_t*>(rest);          // 256
-  uint32_t* off = tot + 256;                                    // 257
-  uint32_t* itemoff = off + 260;                                // 257
-  uint32_t* tsum = itemoff + 260;                               // 1
-  uint32_t* isum = tsum + 4;                                    // 1
+  uint32_t* tot = reinterpret_cast<uint32_t*>(rest);  // 256
+  uint32_t* off = tot + 256;                            // 257
+  uint32_t* itemoff = off + 260;                        // 257
+  uint32_t* tsum = itemoff + 260;                       // 1 (+pad)
+  uint32_t* isum = tsum + 4;                            // 1 (+pad)
   uint32_t* counter = isum + 4;
-  // even number of passes ends in `pairs`
-  uint4* a = reinterpret_cast<uint4*>((key_bytes % 2 == 0) ? pairs : tmp);
-  uint4* b = reinterpret_cast<uint4*>((key_bytes % 2 == 0) ? tmp : pairs);
-  {
-    TraceScope ts(ctx, "k_extract_pairs", st);
-    const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx.sms * 8);
-    k_extract_pairs<<<grid, 256, 0, st>>>(src, n, rec, key_bytes, a);
-    ctx.launches++;
-  }
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx.sms * 2);
+  const size_t smem = kRsTile * (sizeof(uint4) + 1);
+  cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (int byte = (int)key_bytes - 1; byte >= 0; --byte) {
     {
       TraceScope ts(ctx, "k_rs_hist", st);
       k_rs_hist<<<grid, kRsThreads, 0, st>>>(a, n, (uint32_t)byte, ntiles, cnt);
     }
     cudaError_t e = cudaMemsetAsync(tsum, 0, 32, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+    if (e != cudaSuccess) {
+      *status = cuda_fail(ctx, e, "memset");
+      return nullptr;
+    }
     {
       TraceScope ts(ctx, "k_rs_scan", st);
       k_bucket_totals<<<256 / 32, 1024, 0, st>>>(cnt, tot, 256, ntiles, 1u << 30, tsum, isum, ctx.d_err, 1);
@@ -196,15 +195,31 @@ int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, 
     }
     {
       TraceScope ts(ctx, "k_rs_scatter", st);
-      const size_t smem = kRsTile * (sizeof(uint4) + 1);
-      cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_rs_scatter<<<grid, kRsThreads, smem, st>>>(a, b, n, (uint32_t)byte, ntiles, cnt);
     }
     ctx.launches += 4;
     std::swap(a, b);
   }
   cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "sort launch");
+  if (e != cudaSuccess) *status = cuda_fail(ctx, e, "sort launch");
+  return reinterpret_cast<uint8_t*>(a);
+}
+
+int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, uint32_t key_bytes, uint8_t* pairs,
+                    uint8_t* tmp, uint8_t* scan, cudaStream_t st) {
+  if (n == 0) return DPG_OK;
+  // an even number of passes ends where it started
+  uint8_t* start = (key_bytes % 2 == 0) ? pairs : tmp;
+  uint8_t* other = (key_bytes % 2 == 0) ? tmp : pairs;
+  {
+    TraceScope ts(ctx, "k_extract_pairs", st);
+    const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx.sms * 8);
+    k_extract_pairs<<<grid, 256, 0, st>>>(src, n, rec, key_bytes, reinterpret_cast<uint4*>(start));
+    ctx.launches++;
+  }
+  int status = DPG_OK;
+  run_radix_pairs(ctx, start, other, scan, n, key_bytes, st, &status);
+  return status;
 }
 
 }  // namespace dpg

@@ -45,7 +45,10 @@ SIGNATURES = {
     "dpg_retrieve_noalloc": ([_P, _S, _S, _S, _P, _P, _P], _I),
     "dpg_sort_keyptr": ([_P, _P, _S, _S, _S, _P, _P], _I),
     "dpg_sort_records": ([_P, _P, _S, _S, _S, _P, _P], _I),
+    "dpg_fk_join": ([_P, _P, _S, _S, _S, _P, _S, _S, _S, _P, _I, _P], _I),
 }
+
+JOIN_MODES = {"move": 0, "sort": 1, "direct": 2}
 
 
 def _load() -> ctypes.CDLL:
@@ -215,6 +218,23 @@ class Context:
         st = lib.dpg_sort_records(self._h, src.data_ptr(), n_src, rec, key_bytes, out.data_ptr(),
                                   _stream_handle(stream, self.device))
         self._check(st, "dpg_sort_records")
+        return out
+
+    def fk_join(self, fact: torch.Tensor, dim: torch.Tensor, mode: str = "move", fk_off: int = 0, pk_off: int = 0,
+                out: torch.Tensor | None = None, stream=None):
+        """Foreign-key join (§4.2.1): rows fact || dim[fk], by DPG-move, DPG-sort or direct."""
+        _need_cuda(fact, "fact", self.device)
+        _need_cuda(dim, "dim", self.device)
+        n_fact, fb = _table(fact, "fact")
+        n_dim, db = _table(dim, "dim")
+        if out is None:
+            out = torch.empty((n_fact, fb + db), dtype=torch.uint8, device=self.device)
+        _need_cuda(out, "out", self.device)
+        if tuple(out.shape) != (n_fact, fb + db) or out.dtype != torch.uint8:
+            raise ValueError("out must be a uint8 tensor of shape (fact rows, fact bytes + dim bytes)")
+        st = lib.dpg_fk_join(self._h, fact.data_ptr(), n_fact, fb, fk_off, dim.data_ptr(), n_dim, db, pk_off,
+                             out.data_ptr(), JOIN_MODES[mode], _stream_handle(stream, self.device))
+        self._check(st, "dpg_fk_join")
         return out
 
     # -- host buffers (copies in and out happen inside the library)

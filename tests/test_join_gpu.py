@@ -1,0 +1,125 @@
+"""Parity of the GPU foreign-key joins (§4.2.1) with the oracle, byte for byte:
+DPG-move and the direct baseline against oracle.fk_join_move, DPG-sort
+against oracle.fk_join_sorted; Zipf and uniform keys, several row layouts,
+bad keys, and a large sampled case."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_cs_0308004_gb300 import dpg
+    c = dpg.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def relayout(dim, fact, fk, fact_bytes, fk_off, dim_bytes, pk_off, seed=1):
+    """Same keys, other row widths and key offsets."""
+    n_dim, n_fact = dim.shape[0], fact.shape[0]
+    d = synth.records(n_dim, dim_bytes, seed).copy()
+    d[:, pk_off:pk_off + 8] = np.arange(n_dim, dtype="<i8").view(np.uint8).reshape(n_dim, 8)
+    f = synth.records(n_fact, fact_bytes, seed + 1).copy()
+    f[:, fk_off:fk_off + 4] = fk.astype("<i4").view(np.uint8).reshape(n_fact, 4)
+    return d, f
+
+
+def run_all(ctx, dim, fact, fk_off=0, pk_off=0):
+    want_move = oracle.fk_join_move(fact, dim, fk_off, pk_off)
+    want_sort = oracle.fk_join_sorted(fact, dim, fk_off, pk_off)
+    d_dim, d_fact = to_dev(dim), to_dev(fact)
+    for mode, want in (("move", want_move), ("direct", want_move), ("sort", want_sort)):
+        out = torch.full(want.shape, 0xA5, dtype=torch.uint8, device=DEV)
+        ctx.fk_join(d_fact, d_dim, mode, fk_off, pk_off, out=out)
+        ctx.sync()
+        got = out.cpu().numpy()
+        if not np.array_equal(got, want):
+            bad = np.nonzero(np.any(got != want, axis=1))[0]
+            raise AssertionError(f"{mode}: {bad.size} rows differ, first {bad[:5]}")
+
+
+@pytest.mark.parametrize("s", [0.8, 1.3, 0.0])
+@pytest.mark.parametrize("n_dim,n_fact", [(1, 5), (7, 1000), (1000, 100_003), (100_000, 1_000_003), (300, 70_000)])
+def test_join_matches_oracle(ctx, n_dim, n_fact, s):
+    dim, fact, fk = synth.fk_tables(n_dim, n_fact, 64, 16, s, 4 + n_dim)
+    run_all(ctx, dim, fact)
+
+
+@pytest.mark.parametrize("variant", ["2", "4"])
+def test_join_ignores_retrieval_plan(ctx, monkeypatch, variant):
+    """Joins always take the 3-pass DPG retrieval, whatever plan is set."""
+    monkeypatch.setenv("DPG_VARIANT", variant)
+    dim, fact, fk = synth.fk_tables(5000, 200_000, 64, 16, 0.8, 9)
+    run_all(ctx, dim, fact)
+
+
+@pytest.mark.parametrize("fact_bytes,fk_off,dim_bytes,pk_off", [(24, 8, 40, 16), (4, 0, 8, 0), (12, 4, 20, 12),
+                                                                 (64, 60, 256, 248), (16, 12, 100, 3)])
+def test_join_layouts(ctx, fact_bytes, fk_off, dim_bytes, pk_off):
+    dim, fact, fk = synth.fk_tables(20_000, 300_007, 64, 16, 0.8, 5)
+    d, f = relayout(dim, fact, fk, fact_bytes, fk_off, dim_bytes, pk_off)
+    run_all(ctx, d, f, fk_off, pk_off)
+
+
+def test_join_bad_keys(ctx):
+    from paper_cs_0308004_gb300 import dpg
+    dim, fact, fk = synth.fk_tables(1000, 50_000, 64, 16, 0.8, 6)
+    bad = fact.copy()
+    bad[777, :4] = np.array([1000], "<i4").view(np.uint8)        # fk out of range
+    for mode in ("move", "sort", "direct"):
+        out = torch.full((50_000, 80), 0x33, dtype=torch.uint8, device=DEV)
+        ctx.fk_join(to_dev(bad), to_dev(dim), mode, out=out)
+        with pytest.raises(dpg.DpgRangeError):
+            ctx.sync()
+        if mode != "direct":
+            assert bool((out == 0x33).all()), mode
+    dim2 = dim.copy()
+    dim2[int(fk[10]), :8] = np.array([123456], "<i8").view(np.uint8)  # a referenced key is not its row number
+    for mode in ("move", "sort", "direct"):
+        out = torch.full((50_000, 80), 0x33, dtype=torch.uint8, device=DEV)
+        ctx.fk_join(to_dev(fact), to_dev(dim2), mode, out=out)
+        with pytest.raises(dpg.DpgRangeError):
+            ctx.sync()
+        if mode == "move":
+            assert bool((out == 0x33).all())
+    empty_dim = torch.zeros((0, 64), dtype=torch.uint8, device=DEV)
+    for mode in ("move", "sort", "direct"):
+        ctx.fk_join(to_dev(fact[:10]), empty_dim, mode)
+        with pytest.raises(dpg.DpgRangeError):
+            ctx.sync()
+    ctx.sync()
+
+
+def test_join_large_sampled(ctx):
+    """2,000,000 dimension rows x 20,000,000 fact rows, Zipf 0.8: sampled rows
+    of the move join against the oracle; the sort join is the move join's rows
+    in (fk, fact row) order."""
+    n_dim, n_fact = 2_000_000, 20_000_000
+    dim, fact, fk = synth.fk_tables(n_dim, n_fact, 64, 16, 0.8, 4)
+    fact = fact.copy()
+    fact[:, 4:8] = np.arange(n_fact, dtype="<u4").view(np.uint8).reshape(n_fact, 4)  # row ids in the payload
+    d_dim, d_fact = to_dev(dim), to_dev(fact)
+    move = ctx.fk_join(d_fact, d_dim, "move")
+    ctx.sync()
+    idx = np.sort(synth.uniform_ids(20_000, n_fact, 8)).astype(np.int64)
+    want = oracle.fk_join_move(fact[idx], dim)
+    assert np.array_equal(move[torch.from_numpy(idx).to(DEV)].cpu().numpy(), want)
+    srt = ctx.fk_join(d_fact, d_dim, "sort")
+    ctx.sync()
+    rows = srt[:, 4:8].contiguous().view(torch.int32).reshape(-1).long()
+    keys = srt[:, :4].contiguous().view(torch.int32).reshape(-1).long()
+    order = keys * n_fact + rows
+    assert bool((order[1:] > order[:-1]).all())
+    assert torch.equal(srt, move[rows])

@@ -52,6 +52,11 @@ def args_():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sweep-recs", default="16,32,64,100,256", help="record sizes of --sweep")
     p.add_argument("--sweep-impls", default="dpg_smem,dpg_l2,direct", help="implementations of --sweep")
+    p.add_argument("--join", action="store_true",
+                   help="foreign-key join workload (10,000,000 x 64-byte dimension, 200,000,000 x 16-byte fact, "
+                        "Zipf 0.8): DPG-move, DPG-sort and direct; one JSON line; not the headline run")
+    p.add_argument("--n-fact", type=int, default=200_000_000)
+    p.add_argument("--n-dim", type=int, default=10_000_000)
     p.add_argument("--sweep", action="store_true",
                    help="record-size sweep (16/32/64/100/256 B at 1e9 B of source each, permutation rids): "
                         "one JSON line per size, DPG vs direct; not the headline run")
@@ -231,10 +236,66 @@ def run_sweep(a):
     ctx.close()
 
 
+def run_join(a):
+    """Foreign-key joins on the paper's join workload shape (§4.2, §5.3)."""
+    import torch
+    from paper_cs_0308004_gb300 import dpg
+    dev = torch.device("cuda", 0)
+    peak, peak_kind = hbm_peak()
+    t0 = time.time()
+    dim, fact, fk = synth.fk_tables(a.n_dim, a.n_fact, 64, 16, 0.8, 4)
+    t_gen = time.time() - t0
+    ctx = dpg.Context(0)
+    stream = torch.cuda.current_stream(dev)
+    d_dim, d_fact = torch.from_numpy(dim).to(dev), torch.from_numpy(fact).to(dev)
+    d_fk = torch.from_numpy(fk).to(dev)
+    distinct = int(torch.unique(d_fk).numel())
+    del d_fk
+    F = a.n_fact
+    b_comp = F * 16 + distinct * 64 + F * 80
+    b_logical = F * (16 + 64 + 80)
+    out = torch.empty((F, 80), dtype=torch.uint8, device=dev)
+    res = {}
+    for mode in ("move", "sort", "direct"):
+        for _ in range(a.warmup):
+            ctx.fk_join(d_fact, d_dim, mode, out=out)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            ctx.fk_join(d_fact, d_dim, mode, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        ms = e0.elapsed_time(e1) / a.steps
+        ctx.trace_reset()
+        ctx.trace(True)
+        ctx.fk_join(d_fact, d_dim, mode, out=out)
+        torch.cuda.synchronize(dev)
+        kern = {k: round(v[0] / v[1] * 1e3, 1) for k, v in ctx.trace_read().items()}
+        ctx.trace(False)
+        res[mode] = {"ms": round(ms, 3), "gbs_compulsory": round(b_comp / ms / 1e6, 1),
+                     "pct_of_hbm_peak": round(b_comp / ms / 1e6 / peak, 4),
+                     "gbs_logical": round(b_logical / ms / 1e6, 1), "rows_per_s": round(F / ms * 1e3, 1),
+                     "kernels_us": kern}
+    idx = torch.randint(0, F, (4096,), device=dev)
+    fkv = d_fact[idx, :4].contiguous().view(torch.int32).reshape(-1).long()
+    assert torch.equal(out[idx, :16], d_fact[idx]) and torch.equal(out[idx, 16:], d_dim[fkv])
+    print(json.dumps({"impl": "join", "workload": f"fact {F} x 16 B (int32 fk, Zipf 0.8 over shuffled ids, seed 4) "
+                      f"join dim {a.n_dim} x 64 B (int64 pk = row)", "steps": a.steps, "distinct_fk": distinct,
+                      "compulsory_bytes": b_comp, "logical_bytes": b_logical, "peak": peak, "peak_kind": peak_kind,
+                      "input_generation_s": round(t_gen, 1), **res,
+                      "dpg_move_speedup_vs_direct": round(res["direct"]["ms"] / res["move"]["ms"], 4),
+                      "dpg_sort_speedup_vs_direct": round(res["direct"]["ms"] / res["sort"]["ms"], 4)}), flush=True)
+    ctx.close()
+
+
 def main():
     a = args_()
     if a.sweep:
         return run_sweep(a)
+    if a.join:
+        return run_join(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -55,6 +55,13 @@ def args_():
     p.add_argument("--join", action="store_true",
                    help="foreign-key join workload (10,000,000 x 64-byte dimension, 200,000,000 x 16-byte fact, "
                         "Zipf 0.8): DPG-move, DPG-sort and direct; one JSON line; not the headline run")
+    p.add_argument("--batch", action="store_true",
+                   help="batched retrieval workload (4096 requests, record counts log-uniform in [1e3, 1.6e7], "
+                        "record sizes 8..256 B, 70%% permutations / 30%% uniform rids, seed 5) in waves under an "
+                        "HBM budget, each wave one captured CUDA graph; one JSON line; not the headline run")
+    p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--batch-max", type=float, default=1.6e7)
+    p.add_argument("--wave-gb", type=float, default=48.0)
     p.add_argument("--n-fact", type=int, default=200_000_000)
     p.add_argument("--n-dim", type=int, default=10_000_000)
     p.add_argument("--sweep", action="store_true",
@@ -290,10 +297,98 @@ def run_join(a):
     ctx.close()
 
 
+def run_batch(a):
+    """Batched retrieval: waves of requests, each wave one dpg_retrieve_batch
+    captured in a CUDA graph and replayed; the same waves by direct gathers."""
+    import torch
+    from paper_cs_0308004_gb300 import dpg
+    dev = torch.device("cuda", 0)
+    peak, peak_kind = hbm_peak()
+    t0 = time.time()
+    n, rec, kind = synth.batch_requests(a.batch_count, 1e3, a.batch_max, 5)
+    all_rids, offsets = synth.batch_rids(n, n, kind, 5)
+    rows = int(n.max())
+    tables = {r: torch.from_numpy(synth.records(rows, r, 100 + r)).to(dev) for r in synth.BATCH_RECS}
+    t_gen = time.time() - t0
+    ctx = dpg.Context(0)
+    waves, cur, cur_bytes = [], [], 0
+    budget = a.wave_gb * 1e9
+    for k in range(n.size):
+        b = int(n[k]) * int(rec[k])
+        if cur and cur_bytes + b > budget:
+            waves.append(cur)
+            cur, cur_bytes = [], 0
+        cur.append(k)
+        cur_bytes += b
+    if cur:
+        waves.append(cur)
+    tot_ms = tot_ms_direct = 0.0
+    alg = 0
+    launches = []
+    for wave in waves:
+        reqs, groups = [], []
+        for r in synth.BATCH_RECS:
+            ks = [k for k in wave if int(rec[k]) == r]
+            if not ks:
+                continue
+            cat = np.concatenate([all_rids[int(offsets[k]):int(offsets[k]) + int(n[k])] for k in ks])
+            d_rids = torch.from_numpy(cat).to(dev)
+            arena = torch.empty((cat.size, r), dtype=torch.uint8, device=dev)
+            at = 0
+            for k in ks:
+                m = int(n[k])
+                reqs.append((tables[r], m, d_rids[at:at + m], arena[at:at + m]))
+                at += m
+            groups.append((r, d_rids, arena))
+            alg += cat.size * (2 * r + 4)
+        ctx.retrieve_batch(reqs)                      # warm-up sizes the work space
+        ctx.sync()
+        s = torch.cuda.Stream(dev)
+        g = torch.cuda.CUDAGraph()
+        l0 = ctx.kernel_launches
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                ctx.retrieve_batch(reqs, stream=s)
+        launches.append(ctx.kernel_launches - l0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(a.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        tot_ms += e0.elapsed_time(e1) / a.steps
+        for r, d_rids, arena in groups:            # spot check each group
+            idx = torch.randint(0, d_rids.numel(), (1024,), device=dev)
+            assert torch.equal(arena[idx], tables[r][d_rids[idx].long()])
+        e0.record()
+        for _ in range(a.steps):
+            for r, d_rids, arena in groups:
+                ctx.retrieve_direct(tables[r], d_rids, out=arena)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        tot_ms_direct += e0.elapsed_time(e1) / a.steps
+        del g, reqs, groups
+        torch.cuda.empty_cache()
+    print(json.dumps({"impl": "batch", "requests": int(n.size), "records": int(n.sum()),
+                      "dst_bytes": int((n * rec).sum()), "waves": len(waves), "wave_budget_gb": a.wave_gb,
+                      "algorithmic_bytes": alg, "steps": a.steps, "input_generation_s": round(t_gen, 1),
+                      "dpg_batch_ms": round(tot_ms, 3), "dpg_batch_gbs": round(alg / tot_ms / 1e6, 1),
+                      "dpg_pct_of_hbm_peak": round(alg / tot_ms / 1e6 / peak, 4),
+                      "direct_ms": round(tot_ms_direct, 3), "direct_gbs": round(alg / tot_ms_direct / 1e6, 1),
+                      "speedup_vs_direct": round(tot_ms_direct / tot_ms, 4),
+                      "kernels_per_wave_graph": launches, "peak": peak, "peak_kind": peak_kind}), flush=True)
+    ctx.close()
+
+
 def main():
     a = args_()
     if a.sweep:
         return run_sweep(a)
+    if a.batch:
+        return run_batch(a)
     if a.join:
         return run_join(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -145,6 +145,32 @@ dpg_status dpg_fk_join(dpg_ctx* ctx, const void* fact, size_t n_fact, size_t fac
                        const void* dim, size_t n_dim, size_t dim_bytes, size_t pk_off, void* out, int mode,
                        void* stream);
 
+/*
+ * Batched retrieval: `count` requests (a HOST array; its pointers are device
+ * pointers), each dst_k[i] = src_k[rids_k[i]] as in dpg_retrieve, with uneven
+ * record counts and record sizes.  Requests that read the same source table
+ * with the same record size are retrieved together as one DPG run over their
+ * concatenated rid lists, so each source segment is probed once per group
+ * (each rid is still checked against its own request's n_src).  Fastest when
+ * the requests of a group have their rids back to back in one array and their
+ * destinations back to back in one buffer (in request order); otherwise the
+ * call assembles and scatters them in its work space.  Stream-ordered: after
+ * one warm-up call at the same sizes, a batch can be captured in a CUDA graph
+ * (the request table is staged in context-owned pinned memory that a replay
+ * reads again: do not issue other batches on the context between capture and
+ * replay).  The first error of any request is reported by dpg_sync.
+ */
+typedef struct dpg_request {
+  const void* src;      /* n_src records of rec_bytes bytes */
+  size_t n_src;
+  size_t rec_bytes;     /* 1 .. 65536 */
+  size_t n;             /* rids in this request */
+  const int32_t* rids;
+  void* dst;            /* n records */
+} dpg_request;
+
+dpg_status dpg_retrieve_batch(dpg_ctx* ctx, const dpg_request* reqs, size_t count, void* stream);
+
 /* Blocks until `stream` has finished, then returns the first asynchronous
  * error raised by this context's kernels since the previous dpg_sync
  * (DPG_ERANGE, DPG_ETIMEOUT) and clears it; DPG_OK when there was none. */

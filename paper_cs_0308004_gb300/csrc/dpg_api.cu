@@ -193,6 +193,7 @@ void dpg_ctx_destroy(dpg_ctx* c) {
     for (cudaEvent_t e : c->trace_pool) cudaEventDestroy(e);
     if (c->io) cudaFree(c->io);
     if (c->aux) cudaFree(c->aux);
+    if (c->batch_host) cudaFreeHost(c->batch_host);
     if (c->scratch) cudaFree(c->scratch);
     if (c->d_err) cudaFree(c->d_err);
     if (c->h_err) cudaFreeHost(c->h_err);

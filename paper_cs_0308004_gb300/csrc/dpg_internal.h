@@ -29,6 +29,10 @@ struct dpg_ctx {
   // sort or join hands to a retrieval while its own buffers are live)
   void* aux = nullptr;
   size_t aux_bytes = 0;
+  // pinned staging of batch request tables (read again when a captured batch
+  // graph replays)
+  void* batch_host = nullptr;
+  size_t batch_host_bytes = 0;
   // kernel tracing: CUDA events recorded around every launch on its stream
   bool trace = false;
   struct TraceRec {

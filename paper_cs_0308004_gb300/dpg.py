@@ -46,9 +46,16 @@ SIGNATURES = {
     "dpg_sort_keyptr": ([_P, _P, _S, _S, _S, _P, _P], _I),
     "dpg_sort_records": ([_P, _P, _S, _S, _S, _P, _P], _I),
     "dpg_fk_join": ([_P, _P, _S, _S, _S, _P, _S, _S, _S, _P, _I, _P], _I),
+    "dpg_retrieve_batch": ([_P, _P, _S, _P], _I),
 }
 
 JOIN_MODES = {"move": 0, "sort": 1, "direct": 2}
+
+
+class Request(ctypes.Structure):
+    """struct dpg_request (include/dpg.h)."""
+    _fields_ = [("src", ctypes.c_void_p), ("n_src", ctypes.c_size_t), ("rec_bytes", ctypes.c_size_t),
+                ("n", ctypes.c_size_t), ("rids", ctypes.c_void_p), ("dst", ctypes.c_void_p)]
 
 
 def _load() -> ctypes.CDLL:
@@ -236,6 +243,27 @@ class Context:
                              out.data_ptr(), JOIN_MODES[mode], _stream_handle(stream, self.device))
         self._check(st, "dpg_fk_join")
         return out
+
+    def retrieve_batch(self, requests, stream=None):
+        """Batched retrieval.  requests: list of (src, rids, out) device tensors,
+        or (src, n_src, rids, out) to let a request see only the first n_src
+        records of src.  Asynchronous; call sync()."""
+        arr = (Request * max(1, len(requests)))()
+        for k, req in enumerate(requests):
+            if len(req) == 3:
+                src, rids, out = req
+                n_src = src.shape[0]
+            else:
+                src, n_src, rids, out = req
+            for t, nm in ((src, "src"), (rids, "rids"), (out, "out")):
+                _need_cuda(t, nm, self.device)
+            _, rec = _table(src, "src")
+            if rids.dtype != torch.int32 or tuple(out.shape) != (rids.shape[0], rec) or out.dtype != torch.uint8:
+                raise ValueError("each request needs int32 rids and a uint8 out of shape (len(rids), record bytes)")
+            arr[k] = Request(src.data_ptr(), n_src, rec, rids.shape[0], rids.data_ptr(), out.data_ptr())
+        st = lib.dpg_retrieve_batch(self._h, ctypes.cast(arr, ctypes.c_void_p), len(requests),
+                                    _stream_handle(stream, self.device))
+        self._check(st, "dpg_retrieve_batch")
 
     # -- host buffers (copies in and out happen inside the library)
     @staticmethod

@@ -64,6 +64,7 @@ def _load():
             lib.synth_zipf_i32.argtypes = [p, u64, u64, ctypes.c_double, u64]
             lib.synth_zipf_i32.restype = ctypes.c_int
             lib.synth_take_i32.argtypes = [p, p, p, u64]
+            lib.synth_batch_rids.argtypes = [p, p, p, p, p, u64, u64]
             _lib = lib
     return _lib
 
@@ -130,6 +131,19 @@ def take(idx: np.ndarray, table: np.ndarray) -> np.ndarray:
     return out
 
 
+def batch_rids(n: np.ndarray, n_src: np.ndarray, kind: np.ndarray, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """Rid lists of a batch (see synth_batch_rids): returns (all rids, offsets)."""
+    n = np.ascontiguousarray(n, dtype=np.uint64)
+    n_src = np.ascontiguousarray(n_src, dtype=np.uint64)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    offset = np.zeros(n.size, dtype=np.uint64)
+    if n.size:
+        offset[1:] = np.cumsum(n)[:-1]
+    out = np.empty(int(n.sum()), dtype=np.int32)
+    _load().synth_batch_rids(_ptr(out), _ptr(offset), _ptr(n), _ptr(n_src), _ptr(kind), n.size, seed)
+    return out, offset
+
+
 # ---------------------------------------------------------------- workloads
 
 def plain_retrieval(n: int = 1_000_000, rec: int = 100, src_seed: int = 1, rid_seed: int = 2):
@@ -140,6 +154,24 @@ def plain_retrieval(n: int = 1_000_000, rec: int = 100, src_seed: int = 1, rid_s
 def sort_file(n: int = 10_000_000, rec: int = 100, seed: int = 3) -> np.ndarray:
     """n records of rec bytes; the sort key is bytes [0, 10) of each record."""
     return records(n, rec, seed)
+
+
+BATCH_RECS = (8, 16, 32, 64, 100, 128, 256)
+
+
+def batch_requests(count: int = 4096, n_min: float = 1e3, n_max: float = 1.6e7, seed: int = 5,
+                   perm_share: float = 0.7):
+    """Request shapes of the batched-retrieval workload: record counts
+    log-uniform in [n_min, n_max], record sizes uniform over BATCH_RECS, rids
+    a permutation of [0, n) (perm_share of the requests) or uniform draws from
+    [0, n).  Returns (n, rec, kind) arrays; draws come from sub-streams
+    1000+ of `seed` so they do not overlap the rid streams."""
+    u = uniform_f64(count, stream_seed(seed, 1000))
+    n = np.floor(np.exp(np.log(n_min) + u * (np.log(n_max) - np.log(n_min)))).astype(np.uint64)
+    r = uniform_ids(count, len(BATCH_RECS), stream_seed(seed, 1001))
+    rec = np.array(BATCH_RECS, dtype=np.uint64)[r]
+    kind = (uniform_f64(count, stream_seed(seed, 1002)) < perm_share).astype(np.uint8)
+    return n, rec, kind
 
 
 def fk_tables(n_dim: int, n_fact: int, dim_bytes: int = 64, fact_bytes: int = 16,

@@ -105,3 +105,19 @@ void synth_take_i32(int32_t* out, const int32_t* idx, const int32_t* table, uint
 #pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < (int64_t)n; ++k) out[k] = table[idx[k]];
 }
+
+/* Rid lists of a batch of requests, each from its own sub-stream of `seed`:
+ * request k writes n[k] rids at out + offset[k]; kind[k] = 1: a Fisher-Yates
+ * permutation of [0, n[k]) (requires n_src[k] == n[k]), kind[k] = 0: uniform
+ * draws with replacement from [0, n_src[k]).  Requests run in parallel. */
+void synth_batch_rids(int32_t* out, const uint64_t* offset, const uint64_t* n, const uint64_t* n_src,
+                      const uint8_t* kind, uint64_t count, uint64_t seed) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < (int64_t)count; ++k) {
+    const uint64_t s = synth_stream_seed(seed, (uint64_t)k);
+    if (kind[k]) synth_permutation_i32(out + offset[k], n[k], s);
+    else {
+      for (uint64_t t = 0; t < n[k]; ++t) out[offset[k] + t] = (int32_t)mulhi_range(mix64(s + (t + 1) * GOLDEN), n_src[k]);
+    }
+  }
+}

@@ -171,6 +171,57 @@ typedef struct dpg_request {
 
 dpg_status dpg_retrieve_batch(dpg_ctx* ctx, const dpg_request* reqs, size_t count, void* stream);
 
+/*
+ * Serving (the paper has no serving layer; this runs its retrieval and joins
+ * as a request loop).  A server owns `slots` execution slots (a context and a
+ * stream each) on one device and a private stream-ordered memory pool.  Jobs
+ * are queued in submission order; the head of the queue is admitted as soon
+ * as a slot is free and the device memory held by running jobs and by results
+ * not yet released, plus the job's own work space and result, fits within
+ * budget_bytes.  Admitted jobs run concurrently; jobs that arrive while others
+ * run are admitted as slots and memory free up (continuous batching).  A job's
+ * tables are device pointers owned by the caller and must stay valid until
+ * the job completes; its result is allocated by the server, read with
+ * dpg_server_result and freed by dpg_server_release.
+ */
+typedef struct dpg_server dpg_server;
+enum { DPG_JOB_RETRIEVE = 0, DPG_JOB_JOIN = 1 };
+typedef struct dpg_job {
+  int kind;             /* DPG_JOB_RETRIEVE or DPG_JOB_JOIN */
+  int join_mode;        /* DPG_JOIN_* for joins */
+  /* retrieval: result = n records, result[i] = src[rids[i]] (dpg_retrieve) */
+  const void* src;
+  size_t n_src;
+  size_t rec_bytes;
+  size_t n;
+  const int32_t* rids;
+  /* join: result = n_fact rows fact || dim (dpg_fk_join) */
+  const void* fact;
+  size_t n_fact;
+  size_t fact_bytes;
+  size_t fk_off;
+  const void* dim;
+  size_t n_dim;
+  size_t dim_bytes;
+  size_t pk_off;
+} dpg_job;
+
+dpg_status dpg_server_create(dpg_server** out, int device, int slots, size_t budget_bytes);
+/* Queue a job; *ticket identifies it.  DPG_EINVAL for a malformed job,
+ * DPG_EBUSY when the job alone needs more than the budget. */
+dpg_status dpg_server_submit(dpg_server* srv, const dpg_job* job, uint64_t* ticket);
+/* The job's final status (as dpg_sync would report it), its result (device
+ * pointer and size) and its latency from submission to completion.  With
+ * wait == 0 returns DPG_EBUSY while the job is pending. */
+dpg_status dpg_server_result(dpg_server* srv, uint64_t ticket, int wait, void** result, size_t* result_bytes,
+                             double* latency_ms);
+/* Free a completed job's result and forget the ticket. */
+dpg_status dpg_server_release(dpg_server* srv, uint64_t ticket);
+/* Device bytes currently held by running jobs and unreleased results. */
+size_t dpg_server_held_bytes(dpg_server* srv);
+/* Finish running jobs (queued ones are dropped), free everything. */
+void dpg_server_destroy(dpg_server* srv);
+
 /* Blocks until `stream` has finished, then returns the first asynchronous
  * error raised by this context's kernels since the previous dpg_sync
  * (DPG_ERANGE, DPG_ETIMEOUT) and clears it; DPG_OK when there was none. */

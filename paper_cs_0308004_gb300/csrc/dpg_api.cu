@@ -96,6 +96,10 @@ static void trace_collect(dpg_ctx& ctx) {
 
 int ensure_scratch(dpg_ctx& ctx, size_t bytes) {
   if (bytes <= ctx.scratch_bytes) return DPG_OK;
+  if (ctx.external_memory) {
+    ctx.last_error = "lent scratch too small";
+    return DPG_ENOMEM;
+  }
   const size_t grain = size_t(2) << 20;
   const size_t want = (bytes + grain - 1) / grain * grain;
   if (ctx.scratch) {
@@ -117,6 +121,10 @@ int ensure_scratch(dpg_ctx& ctx, size_t bytes) {
 
 int ensure_aux(dpg_ctx& ctx, size_t bytes) {
   if (bytes <= ctx.aux_bytes) return DPG_OK;
+  if (ctx.external_memory) {
+    ctx.last_error = "lent work space too small";
+    return DPG_ENOMEM;
+  }
   const size_t grain = size_t(2) << 20;
   const size_t want = (bytes + grain - 1) / grain * grain;
   if (ctx.aux) {
@@ -192,9 +200,9 @@ void dpg_ctx_destroy(dpg_ctx* c) {
     }
     for (cudaEvent_t e : c->trace_pool) cudaEventDestroy(e);
     if (c->io) cudaFree(c->io);
-    if (c->aux) cudaFree(c->aux);
+    if (c->aux && !c->external_memory) cudaFree(c->aux);
     if (c->batch_host) cudaFreeHost(c->batch_host);
-    if (c->scratch) cudaFree(c->scratch);
+    if (c->scratch && !c->external_memory) cudaFree(c->scratch);
     if (c->d_err) cudaFree(c->d_err);
     if (c->h_err) cudaFreeHost(c->h_err);
   }

@@ -20,6 +20,7 @@ struct dpg_ctx {
   int* h_err = nullptr;      // pinned host copy used by dpg_sync
   void* scratch = nullptr;   // grown on demand
   size_t scratch_bytes = 0;
+  bool external_memory = false;  // scratch and aux lent by a server: never grown or freed here
   uint64_t launches = 0;
   std::string last_error;
   // host-buffer entry points: device copies of the caller's tables
@@ -106,6 +107,9 @@ constexpr uint32_t kSmemBuckets = 24576;      // Phase I per-CTA counters fit in
 // Plan chosen for a retrieval (environment overrides DPG_VARIANT,
 // DPG_SEG_LOG2, DPG_CHUNK apply when set).
 Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r);
+
+// Bytes of context scratch a retrieval will take (its plan as chosen now).
+size_t retrieve_scratch_need(const dpg_ctx& ctx, const Retrieval& r);
 
 // Enqueue the DPG retrieval / the direct gather.  Return a dpg_status.
 int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan);

@@ -681,29 +681,50 @@ void launch_probe(dpg_ctx& ctx, uint32_t WB, const Retrieval& r, uint32_t seg_lo
 
 int run_dpg_l2(dpg_ctx& ctx, const Retrieval& r, const Plan& plan);
 
+// Scratch layout of the shared-memory-segment plans (variants 2 and 3), each
+// piece 256-byte aligned.
+struct Layout3 {
+  uint32_t sl, nb, grid, G, chunk;
+  uint64_t S, per;
+  bool smem_mode, three, strided;
+  size_t b_cnt, b_tot, b_off, b_ctr, b_lo, b_side, b_ts, b_rc, b_stage, need;
+};
+
+Layout3 layout3(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, size_t lo_size, bool strided) {
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  Layout3 L;
+  L.sl = (uint32_t)plan.seg_log2;
+  L.S = 1ull << L.sl;
+  L.nb = (uint32_t)((r.n_src + L.S - 1) >> L.sl);
+  L.smem_mode = L.nb <= kSmemBuckets;
+  L.grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)ctx.sms * 2, (r.n + 8191) / 8192));
+  L.G = L.smem_mode ? L.grid : 1;
+  L.per = (r.n + L.grid - 1) / L.grid;
+  L.chunk = plan.chunk ? plan.chunk : (uint32_t)std::min<uint64_t>(4 * L.S, 1u << 20);
+  L.three = plan.variant != 2 || r.join != nullptr;
+  L.strided = strided;
+  L.b_cnt = al((size_t)L.nb * L.G * 4);
+  L.b_tot = al((size_t)L.nb * 4);
+  L.b_off = al(((size_t)L.nb + 1) * 4);
+  L.b_ctr = 256;
+  L.b_lo = al(r.n * lo_size);
+  L.b_side = al(r.n * 4);
+  L.b_ts = al((size_t)((L.nb + kScanTile - 1) / kScanTile) * 4);
+  L.b_rc = strided ? al(r.n * 4) : 0;  // rids copied out of strided pairs by Phase I pass 1
+  L.b_stage = L.three ? al(r.n * r.rec) : 0;
+  L.need = L.b_cnt + L.b_tot + 2 * L.b_off + L.b_ctr + 2 * L.b_ts + L.b_lo + L.b_side + L.b_rc + L.b_stage;
+  return L;
+}
+
 template <class Rid, typename LoT>
 int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
-  const uint32_t sl = (uint32_t)plan.seg_log2;
-  const uint64_t S = 1ull << sl;
-  const uint32_t nb = (uint32_t)((r.n_src + S - 1) >> sl);
-  const bool smem_mode = nb <= kSmemBuckets;
-  const uint32_t grid = (uint32_t)std::max<uint64_t>(
-      1, std::min<uint64_t>((uint64_t)ctx.sms * 2, (r.n + 8191) / 8192));
-  const uint32_t G = smem_mode ? grid : 1;
-  const uint64_t per = (r.n + grid - 1) / grid;
-  const uint32_t chunk = plan.chunk ? plan.chunk : (uint32_t)std::min<uint64_t>(4 * S, 1u << 20);
-  const bool three = plan.variant != 2 || r.join != nullptr;
-
-  // scratch layout, each piece 256-byte aligned
-  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t b_cnt = al((size_t)nb * G * 4), b_tot = al((size_t)nb * 4), b_off = al(((size_t)nb + 1) * 4);
-  const size_t b_ctr = 256, b_lo = al(r.n * sizeof(LoT)), b_side = al(r.n * 4);
-  const size_t b_ts = al((size_t)((nb + kScanTile - 1) / kScanTile) * 4);
-  const bool strided = !std::is_same<Rid, RidArray>::value;
-  const size_t b_rc = strided ? al(r.n * 4) : 0;  // rids copied out of strided pairs by Phase I pass 1
-  const size_t b_stage = three ? al(r.n * r.rec) : 0;
-  const size_t need = b_cnt + b_tot + 2 * b_off + b_ctr + 2 * b_ts + b_lo + b_side + b_rc + b_stage;
-  if (int s = ensure_scratch(ctx, need)) return s;
+  const Layout3 L = layout3(ctx, r, plan, sizeof(LoT), !std::is_same<Rid, RidArray>::value);
+  const uint32_t sl = L.sl, nb = L.nb, grid = L.grid, G = L.G, chunk = L.chunk;
+  const uint64_t S = L.S, per = L.per;
+  const bool smem_mode = L.smem_mode, three = L.three, strided = L.strided;
+  const size_t b_cnt = L.b_cnt, b_tot = L.b_tot, b_off = L.b_off, b_ctr = L.b_ctr, b_lo = L.b_lo,
+               b_side = L.b_side, b_ts = L.b_ts, b_rc = L.b_rc;
+  if (int s = ensure_scratch(ctx, L.need)) return s;
   uint8_t* p = static_cast<uint8_t*>(ctx.scratch);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(p); p += b_cnt;
   uint32_t* tot = reinterpret_cast<uint32_t*>(p); p += b_tot;
@@ -796,6 +817,16 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
 
 // Variant 4 (L2 runs): k_hist -> k_bucket_totals -> k_scan -> k_partition ->
 // k_probe_l2 -> k_gather_phase3.
+size_t layout4_need(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool strided) {
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const uint64_t S = 1ull << plan.seg_log2;
+  const uint32_t nb = (uint32_t)((r.n_src + S - 1) >> plan.seg_log2);
+  const uint32_t G = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)ctx.sms * 2, (r.n + 8191) / 8192));
+  return al((size_t)nb * G * 4) + al((size_t)nb * 4) + 2 * al(((size_t)nb + 1) * 4) + 2 * 256 +
+         2 * al((size_t)((nb + kScanTile - 1) / kScanTile) * 4) + 2 * al(r.n * 4) + (strided ? al(r.n * 4) : 0) +
+         al(r.n * r.rec);
+}
+
 template <class Rid>
 int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   const uint32_t sl = (uint32_t)plan.seg_log2;
@@ -811,8 +842,7 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   const size_t b_cnt = al((size_t)nb * G * 4), b_tot = al((size_t)nb * 4), b_off = al(((size_t)nb + 1) * 4);
   const size_t b_ctr = 256, b_ts = al((size_t)((nb + kScanTile - 1) / kScanTile) * 4);
   const size_t b_run = al(r.n * 4), b_slot = al(r.n * 4), b_rc = strided ? al(r.n * 4) : 0;
-  const size_t b_stage = al(r.n * r.rec);
-  const size_t need = b_cnt + b_tot + 2 * b_off + 2 * b_ctr + 2 * b_ts + b_run + b_slot + b_rc + b_stage;
+  const size_t need = layout4_need(ctx, r, plan, strided);
   if (int s = ensure_scratch(ctx, need)) return s;
   uint8_t* p = static_cast<uint8_t*>(ctx.scratch);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(p); p += b_cnt;
@@ -917,6 +947,14 @@ Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
     p.seg_log2 = k;
   }
   return p;
+}
+
+size_t retrieve_scratch_need(const dpg_ctx& ctx, const Retrieval& r) {
+  if (r.n == 0 || r.n_src == 0) return 0;
+  const Plan plan = choose_plan(ctx, r);
+  const bool strided = r.rids.stride != 4;
+  if (plan.variant == 4 && !r.join) return layout4_need(ctx, r, plan, strided);
+  return layout3(ctx, r, plan, plan.seg_log2 <= 16 ? 2 : 4, strided).need;
 }
 
 int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {

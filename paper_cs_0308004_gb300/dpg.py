@@ -47,9 +47,26 @@ SIGNATURES = {
     "dpg_sort_records": ([_P, _P, _S, _S, _S, _P, _P], _I),
     "dpg_fk_join": ([_P, _P, _S, _S, _S, _P, _S, _S, _S, _P, _I, _P], _I),
     "dpg_retrieve_batch": ([_P, _P, _S, _P], _I),
+    "dpg_server_create": ([ctypes.POINTER(ctypes.c_void_p), _I, _I, _S], _I),
+    "dpg_server_submit": ([_P, _P, ctypes.POINTER(ctypes.c_uint64)], _I),
+    "dpg_server_result": ([_P, ctypes.c_uint64, _I, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t),
+                           ctypes.POINTER(ctypes.c_double)], _I),
+    "dpg_server_release": ([_P, ctypes.c_uint64], _I),
+    "dpg_server_held_bytes": ([_P], _S),
+    "dpg_server_destroy": ([_P], None),
 }
 
 JOIN_MODES = {"move": 0, "sort": 1, "direct": 2}
+
+
+class Job(ctypes.Structure):
+    """struct dpg_job (include/dpg.h)."""
+    _fields_ = [("kind", ctypes.c_int), ("join_mode", ctypes.c_int),
+                ("src", ctypes.c_void_p), ("n_src", ctypes.c_size_t), ("rec_bytes", ctypes.c_size_t),
+                ("n", ctypes.c_size_t), ("rids", ctypes.c_void_p),
+                ("fact", ctypes.c_void_p), ("n_fact", ctypes.c_size_t), ("fact_bytes", ctypes.c_size_t),
+                ("fk_off", ctypes.c_size_t), ("dim", ctypes.c_void_p), ("n_dim", ctypes.c_size_t),
+                ("dim_bytes", ctypes.c_size_t), ("pk_off", ctypes.c_size_t)]
 
 
 class Request(ctypes.Structure):
@@ -312,3 +329,88 @@ class Context:
     def sync(self, stream=None):
         """Wait for the stream; raise the first asynchronous error (bad rid, timeout)."""
         self._check(lib.dpg_sync(self._h, _stream_handle(stream, self.device)), "dpg_sync")
+
+
+class _DeviceBytes:
+    """A device buffer seen by torch through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "|u1", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Server:
+    """Request loop with HBM-budget admission (dpg_server_* in include/dpg.h)."""
+
+    def __init__(self, device: int = 0, slots: int = 4, budget_bytes: int = 8 << 30):
+        self.device = torch.device("cuda", device)
+        h = ctypes.c_void_p()
+        st = lib.dpg_server_create(ctypes.byref(h), device, slots, budget_bytes)
+        if st != OK:
+            raise DpgError(st, "dpg_server_create")
+        self._h = h
+        self._shapes = {}
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.dpg_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _submit(self, job: Job, shape, keep) -> int:
+        t = ctypes.c_uint64()
+        st = lib.dpg_server_submit(self._h, ctypes.byref(job), ctypes.byref(t))
+        if st != OK:
+            raise DpgError(st, "dpg_server_submit")
+        self._shapes[t.value] = shape
+        self._keep[t.value] = keep          # the tables must outlive the job
+        return t.value
+
+    def submit_retrieve(self, src: torch.Tensor, rids: torch.Tensor, n_src: int | None = None) -> int:
+        n_src_all, rec = _table(src, "src")
+        job = Job(kind=0, src=src.data_ptr(), n_src=n_src_all if n_src is None else n_src, rec_bytes=rec,
+                  n=rids.shape[0], rids=rids.data_ptr())
+        return self._submit(job, (rids.shape[0], rec), (src, rids))
+
+    def submit_join(self, fact: torch.Tensor, dim: torch.Tensor, mode: str = "move", fk_off: int = 0,
+                    pk_off: int = 0) -> int:
+        n_fact, fb = _table(fact, "fact")
+        n_dim, db = _table(dim, "dim")
+        job = Job(kind=1, join_mode=JOIN_MODES[mode], fact=fact.data_ptr(), n_fact=n_fact, fact_bytes=fb,
+                  fk_off=fk_off, dim=dim.data_ptr(), n_dim=n_dim, dim_bytes=db, pk_off=pk_off)
+        return self._submit(job, (n_fact, fb + db), (fact, dim))
+
+    def result(self, ticket: int, wait: bool = True):
+        """(status, result tensor viewing server memory or None, latency ms); None while pending."""
+        p, nbytes, lat = ctypes.c_void_p(), ctypes.c_size_t(), ctypes.c_double()
+        st = lib.dpg_server_result(self._h, ticket, 1 if wait else 0, ctypes.byref(p), ctypes.byref(nbytes),
+                                   ctypes.byref(lat))
+        if st == EBUSY and not wait:
+            return None
+        shape = self._shapes[ticket]
+        out = None
+        if p.value and shape[0] * shape[1]:
+            out = torch.as_tensor(_DeviceBytes(p.value, shape), device=self.device)
+        return st, out, lat.value
+
+    def release(self, ticket: int):
+        lib.dpg_server_release(self._h, ticket)
+        self._shapes.pop(ticket, None)
+        self._keep.pop(ticket, None)
+
+    @property
+    def held_bytes(self) -> int:
+        return int(lib.dpg_server_held_bytes(self._h))

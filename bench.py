@@ -62,6 +62,15 @@ def args_():
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--batch-max", type=float, default=1.6e7)
     p.add_argument("--wave-gb", type=float, default=48.0)
+    p.add_argument("--serve", action="store_true",
+                   help="serving workload: Poisson arrivals (mean 2000 req/s), 60%% retrievals / 40%% joins, "
+                        "rows log-uniform in [1e4, 5e7], record sizes 16..256 B, resident tables, 120 GB "
+                        "admission budget; p50/p99 latency and aggregate GB/s; one JSON line")
+    p.add_argument("--serve-seconds", type=float, default=10.0)
+    p.add_argument("--serve-rate", type=float, default=2000.0)
+    p.add_argument("--serve-rows", type=int, default=50_000_000)
+    p.add_argument("--serve-slots", type=int, default=8)
+    p.add_argument("--serve-budget-gb", type=float, default=120.0)
     p.add_argument("--n-fact", type=int, default=200_000_000)
     p.add_argument("--n-dim", type=int, default=10_000_000)
     p.add_argument("--sweep", action="store_true",
@@ -383,8 +392,111 @@ def run_batch(a):
     ctx.close()
 
 
+def run_serve(a):
+    """Open-loop serving: requests arrive as a Poisson process and are
+    submitted to a dpg_server; results are released as they complete."""
+    import torch
+    from paper_cs_0308004_gb300 import dpg
+    dev = torch.device("cuda", 0)
+    R = a.serve_rows
+    recs = (16, 32, 64, 100, 128, 256)
+    t0 = time.time()
+    tables = {r: torch.from_numpy(synth.records(R, r, 500 + r)).to(dev) for r in recs}
+    perm = torch.from_numpy(synth.permutation(R, 501)).to(dev)
+    dim, fact, _ = synth.fk_tables(10_000_000, R, 64, 16, 0.8, 4)
+    d_dim, d_fact = torch.from_numpy(dim).to(dev), torch.from_numpy(fact).to(dev)
+    del dim, fact
+    t_setup = time.time() - t0
+    # the request stream (seed 6): arrival gaps, kind, rows, record size, offset, join mode
+    count = int(a.serve_rate * a.serve_seconds)
+    gaps = -np.log(1.0 - synth.uniform_f64(count, synth.stream_seed(6, 0))) / a.serve_rate
+    arrive = np.cumsum(gaps)
+    is_join = synth.uniform_f64(count, synth.stream_seed(6, 1)) < 0.4
+    u = synth.uniform_f64(count, synth.stream_seed(6, 2))
+    rows = np.floor(np.exp(np.log(1e4) + u * (np.log(min(5e7, R)) - np.log(1e4)))).astype(np.int64)
+    rec_pick = synth.uniform_ids(count, len(recs), synth.stream_seed(6, 3))
+    start = (synth.uniform_f64(count, synth.stream_seed(6, 4)) * (R - rows + 1)).astype(np.int64)
+    mode_pick = synth.uniform_ids(count, 2, synth.stream_seed(6, 5))
+    srv = dpg.Server(0, slots=a.serve_slots, budget_bytes=int(a.serve_budget_gb * 1e9))
+    pending, lat, done_bytes, statuses = {}, [], 0, {}
+    first_submit = last_done = None
+    sample = set(int(x) for x in synth.uniform_ids(16, count, synth.stream_seed(6, 6)))
+    kept = {}
+
+    def job_bytes(k):
+        n = int(rows[k])
+        if is_join[k]:
+            return n * (16 + 64 + 80)
+        r = recs[int(rec_pick[k])]
+        return n * (2 * r + 4)
+
+    def reap(block):
+        nonlocal done_bytes, last_done
+        for k in list(pending)[:16]:          # oldest first: jobs finish roughly in order
+            res = srv.result(pending[k], wait=block)
+            if res is None:
+                continue
+            st, out, ms = res
+            statuses[st] = statuses.get(st, 0) + 1
+            lat.append(ms)
+            done_bytes += job_bytes(k)
+            last_done = time.perf_counter()
+            if k in sample and out is not None:
+                kept[k] = out.clone()
+            srv.release(pending.pop(k))
+            if block:
+                return
+
+    base = time.perf_counter()
+    for k in range(count):
+        while time.perf_counter() - base < arrive[k]:
+            reap(False)
+        n, s0 = int(rows[k]), int(start[k])
+        if is_join[k]:
+            t = srv.submit_join(d_fact[s0:s0 + n], d_dim, "move" if mode_pick[k] == 0 else "sort")
+        else:
+            t = srv.submit_retrieve(tables[recs[int(rec_pick[k])]], perm[s0:s0 + n])
+        if first_submit is None:
+            first_submit = time.perf_counter()
+        pending[k] = t
+    while pending:
+        reap(True)
+    wall = last_done - first_submit
+    # seeded sample: spot rows against the tables, and the same job alone
+    checked = 0
+    for k, out in kept.items():
+        n, s0 = int(rows[k]), int(start[k])
+        idx = torch.randint(0, n, (256,), device=dev)
+        if is_join[k]:
+            if mode_pick[k] == 0:
+                fk = d_fact[s0 + idx, :4].contiguous().view(torch.int32).reshape(-1).long()
+                assert torch.equal(out[idx, :16], d_fact[s0 + idx]) and torch.equal(out[idx, 16:], d_dim[fk])
+            t = srv.submit_join(d_fact[s0:s0 + n], d_dim, "move" if mode_pick[k] == 0 else "sort")
+        else:
+            tab = tables[recs[int(rec_pick[k])]]
+            assert torch.equal(out[idx], tab[perm[s0 + idx].long()])
+            t = srv.submit_retrieve(tab, perm[s0:s0 + n])
+        st, alone, _ = srv.result(t)
+        assert st == dpg.OK and torch.equal(alone, out), "result differs alone and in the mix"
+        srv.release(t)
+        checked += 1
+    srv.close()
+    lat_a = np.array(lat)
+    offered = sum(job_bytes(k) for k in range(count)) / arrive[-1] / 1e9
+    print(json.dumps({"impl": "serve", "requests": count, "seconds_of_arrivals": round(float(arrive[-1]), 2),
+                      "rate_req_s": a.serve_rate, "slots": a.serve_slots, "budget_gb": a.serve_budget_gb,
+                      "offered_gbs": round(offered, 1), "aggregate_gbs": round(done_bytes / wall / 1e9, 1),
+                      "wall_s": round(wall, 2), "p50_ms": round(float(np.percentile(lat_a, 50)), 3),
+                      "p99_ms": round(float(np.percentile(lat_a, 99)), 3), "mean_ms": round(float(lat_a.mean()), 3),
+                      "statuses": {str(k): v for k, v in statuses.items()},
+                      "verified_alone_vs_mix": checked, "setup_s": round(t_setup, 1),
+                      "bytes": "retrieval n*(2*rec+4); join n*(16+64+80) logical"}), flush=True)
+
+
 def main():
     a = args_()
+    if a.serve:
+        return run_serve(a)
     if a.sweep:
         return run_sweep(a)
     if a.batch:

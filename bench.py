@@ -51,7 +51,7 @@ def args_():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sweep-recs", default="16,32,64,100,256", help="record sizes of --sweep")
-    p.add_argument("--sweep-impls", default="dpg_smem,dpg_l2,direct", help="implementations of --sweep")
+    p.add_argument("--sweep-impls", default="dpg_smem,dpg_l2,dpg_tuned,direct", help="implementations of --sweep")
     p.add_argument("--join", action="store_true",
                    help="foreign-key join workload (10,000,000 x 64-byte dimension, 200,000,000 x 16-byte fact, "
                         "Zipf 0.8): DPG-move, DPG-sort and direct; one JSON line; not the headline run")
@@ -209,12 +209,15 @@ def run_sweep(a):
         d_rids = torch.from_numpy(rids).to(dev)
         out = torch.empty((n, rec), dtype=torch.uint8, device=dev)
         res, kern = {}, {}
+        tuned = ctx.tune(d_src, d_rids, out) if "dpg_tuned" in a.sweep_impls.split(",") else None
         for name, variant, fn in (("dpg_smem", "3", ctx.retrieve), ("dpg_l2", "4", ctx.retrieve),
-                                  ("direct", None, ctx.retrieve_direct)):
+                                  ("dpg_tuned", "", ctx.retrieve), ("direct", None, ctx.retrieve_direct)):
             if name not in a.sweep_impls.split(","):
                 continue
             if variant:
                 os.environ["DPG_VARIANT"] = variant
+            else:
+                os.environ.pop("DPG_VARIANT", None)
             for _ in range(a.warmup):
                 fn(d_src, d_rids, out=out)
             ctx.sync()
@@ -228,7 +231,7 @@ def run_sweep(a):
             res[name] = e0.elapsed_time(e1) / a.steps
             idx = torch.randint(0, n, (4096,), device=dev)
             assert torch.equal(out[idx], d_src[d_rids[idx].long()])
-            if variant:
+            if variant is not None:
                 ctx.trace_reset()
                 ctx.trace(True)
                 for _ in range(3):
@@ -242,7 +245,9 @@ def run_sweep(a):
         for name, ms in res.items():
             line[f"{name}_gbs"] = round(b / ms / 1e6, 1)
             line[f"{name}_ms"] = round(ms, 4)
-        for name in ("dpg_smem", "dpg_l2"):
+        if tuned:
+            line["tuned_plan"] = {"variant": tuned[0], "seg_log2": tuned[1]}
+        for name in ("dpg_smem", "dpg_l2", "dpg_tuned"):
             if name in res and "direct" in res:
                 line[f"{name}_speedup_vs_direct"] = round(res["direct"] / res[name], 4)
         line["kernels_us"] = kern
@@ -601,6 +606,9 @@ def main():
     assert torch.equal(g_pairs, d_pairs), "GPU key-pointer sort differs from the host-prepared pairs"
     del g_pairs
 
+    # pick the DPG plan for this shape by timing the candidates (outside the timed region)
+    plan = ctx.tune(d_src, d_pairs, d_out, rid_stride=16, rid_off=12)
+
     ms_dpg, launches, win = timed(lambda: ctx.sort_copy(d_pairs, d_src, out=d_out))
     ms_dir, launches_dir, win_dir = timed(lambda: ctx.sort_copy_direct(d_pairs, d_src, out=d_out))
 
@@ -673,6 +681,8 @@ def main():
             "config": {"workload": WORKLOAD, "n": n, "rec_bytes": rec, "pairs_bytes": 16,
                        "algorithmic_bytes_per_step": alg_bytes,
                        "l2": "inputs larger than L2 (2.16 GB read/written per step vs 126 MB L2); no flush",
+                       "plan": {"variant": plan[0], "seg_log2": plan[1],
+                                "picked_by": "dpg_tune (CUDA-event timing of the candidate plans)"},
                        "parallelism": f"replicas x{world}"},
             "pct_of_hbm_peak": round(value / world / peak, 4),
             "records_per_s": round(world * n / (ms_dpg * 1e-3), 1),

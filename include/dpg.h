@@ -245,6 +245,25 @@ dpg_status dpg_sort_copy_host(dpg_ctx* ctx, const void* pairs, size_t pair_strid
                               void* stream);
 
 /*
+ * Plan tuning (the paper fixes the run length to half the cache, §2.1; on a
+ * GPU the best run length and plan depend on the record size and the table
+ * sizes, so they are measured).  dpg_tune runs each candidate plan for this
+ * retrieval shape on the caller's data (rids at rid_base, rid_stride bytes
+ * apart: 4 for an int32 array, 16 with rid_off 12 for key-pointer pairs;
+ * dst receives the result), times them with CUDA events on `stream`, and
+ * caches the fastest in the context for retrievals of the same record size,
+ * size classes (log2 of n_src and n) and rid layout.  Blocking.  Candidates:
+ * the 3-pass plan with shared-memory segments of the largest power-of-two
+ * record count that fits 104 KB and of one half and one quarter of it, the
+ * 2-pass plan, and the L2-run plan with runs of about 4 MB and 16 MB.
+ * *variant (3, 2 or 4) and *seg_log2 receive the winner (may be NULL).
+ * dpg_last_plan reports the plan of the context's last retrieval.
+ */
+dpg_status dpg_tune(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes, size_t n, const void* rid_base,
+                    size_t rid_stride, void* dst, void* stream, int* variant, int* seg_log2);
+void dpg_last_plan(dpg_ctx* ctx, int* variant, int* seg_log2);
+
+/*
  * Kernel tracing (measurement support; the paper has none).  While enabled,
  * every kernel the context launches is bracketed by two CUDA events recorded
  * on its stream.  dpg_trace_count / dpg_trace_get wait for the recorded

@@ -325,6 +325,67 @@ dpg_status dpg_sort_records(dpg_ctx* c, const void* src, size_t n_src, size_t re
   return (dpg_status)dpg::run_dpg(*c, r, dpg::choose_plan(*c, r));
 }
 
+// ---- plan tuning
+
+dpg_status dpg_tune(dpg_ctx* c, const void* src, size_t n_src, size_t rec, size_t n, const void* rid_base,
+                    size_t rid_stride, void* dst, void* stream, int* variant, int* seg_log2) {
+  if (rid_stride < 4 || rid_stride % 4) return DPG_EINVAL;
+  int s = check_retrieval(c, src, n_src, rec, n, rid_base, n * rid_stride, dst);
+  if (s != DPG_OK) return (dpg_status)s;
+  if (n == 0 || n_src == 0 || rec > dpg::kMaxDpgRecBytes || reinterpret_cast<uintptr_t>(rid_base) % 4)
+    return n == 0 ? DPG_OK : DPG_EINVAL;
+  DeviceGuard g(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  dpg::Retrieval r{static_cast<const uint8_t*>(src), n_src, (uint32_t)rec, n,
+                   dpg::RidSpec{static_cast<const uint8_t*>(rid_base), (uint32_t)rid_stride},
+                   static_cast<uint8_t*>(dst), st};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return DPG_ECUDA;
+  }
+  const bool was_tracing = c->trace;
+  c->trace = false;
+  float best = 1e30f;
+  dpg::Plan best_plan;
+  int rc = DPG_OK;
+  for (const dpg::Plan& p : dpg::plan_candidates(*c, r)) {
+    rc = dpg::run_dpg(*c, r, p);  // warm-up, sizes the scratch
+    if (rc == DPG_OK) rc = dpg_sync(c, stream);
+    if (rc != DPG_OK) break;
+    float total = 0.f;
+    for (int rep = 0; rep < 2 && rc == DPG_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      rc = dpg::run_dpg(*c, r, p);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      total += ms;
+    }
+    if (rc == DPG_OK) rc = dpg_sync(c, stream);
+    if (rc != DPG_OK) break;
+    if (total < best) {
+      best = total;
+      best_plan = p;
+    }
+  }
+  c->trace = was_tracing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != DPG_OK) return (dpg_status)rc;
+  c->plans[dpg::plan_key(r)] = {best_plan.variant, best_plan.seg_log2};
+  if (variant) *variant = best_plan.variant;
+  if (seg_log2) *seg_log2 = best_plan.seg_log2;
+  return DPG_OK;
+}
+
+void dpg_last_plan(dpg_ctx* c, int* variant, int* seg_log2) {
+  if (!c) return;
+  if (variant) *variant = c->last_variant;
+  if (seg_log2) *seg_log2 = c->last_seg_log2;
+}
+
 void dpg_trace_enable(dpg_ctx* c, int on) {
   if (!c) return;
   DeviceGuard g(c->device);

@@ -44,6 +44,9 @@ struct dpg_ctx {
   std::vector<cudaEvent_t> trace_pool;
   std::map<std::string, std::pair<double, uint64_t>> trace_totals;  // name -> (ms, launches)
   std::vector<std::string> trace_names;                              // stable order for readers
+  // plans chosen by dpg_tune, keyed by retrieval shape, and the last plan run
+  std::map<uint64_t, std::pair<int, int>> plans;  // key -> (variant, seg_log2)
+  int last_variant = 0, last_seg_log2 = 0;
 };
 
 namespace dpg {
@@ -104,9 +107,13 @@ struct Retrieval {
 constexpr uint32_t kMaxDpgRecBytes = 65536;   // a segment holds at least one record
 constexpr uint32_t kSmemBuckets = 24576;      // Phase I per-CTA counters fit in 96 KB
 
-// Plan chosen for a retrieval (environment overrides DPG_VARIANT,
-// DPG_SEG_LOG2, DPG_CHUNK apply when set).
+// Plan chosen for a retrieval: environment overrides (DPG_VARIANT,
+// DPG_SEG_LOG2, DPG_CHUNK, DPG_L2_RUN_KB) when set, else a plan dpg_tune
+// cached for the retrieval's shape, else the default for its record size.
 Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r);
+uint64_t plan_key(const Retrieval& r);
+// Candidate plans the tuner times for a retrieval.
+std::vector<Plan> plan_candidates(const dpg_ctx& ctx, const Retrieval& r);
 
 // Bytes of context scratch a retrieval will take (its plan as chosen now).
 size_t retrieve_scratch_need(const dpg_ctx& ctx, const Retrieval& r);

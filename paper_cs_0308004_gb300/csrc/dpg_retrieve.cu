@@ -925,28 +925,81 @@ int run_dpg_l2(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {
 
 }  // namespace
 
-Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
-  (void)ctx;
-  Plan p;
+namespace {
+
+int smem_seg_log2(const Retrieval& r) {
   int sl = 0;
   while (sl < 30 && ((2ull << sl) * r.rec) <= kSegBytesMax) ++sl;
-  // keep the number of segments within the shared-memory counters if possible
-  p.seg_log2 = sl;
+  return sl;
+}
+
+// Runs of about run_bytes of source for the L2-run plan, at most kPartMaxRuns.
+int l2_seg_log2(const Retrieval& r, uint64_t run_bytes) {
+  int k = 0;
+  while (k < 31 && ((2ull << k) * r.rec) <= run_bytes) ++k;
+  while (k < 31 && ((r.n_src + (1ull << k) - 1) >> k) > kPartMaxRuns) ++k;
+  return k;
+}
+
+int ilog2(uint64_t x) {
+  int k = 0;
+  while (x >>= 1) ++k;
+  return k;
+}
+
+}  // namespace
+
+uint64_t plan_key(const Retrieval& r) {
+  return ((uint64_t)r.rec << 32) | ((uint64_t)ilog2(r.n_src + 1) << 24) | ((uint64_t)ilog2(r.n + 1) << 16) |
+         ((uint64_t)(r.rids.stride != 4) << 8) | (uint64_t)(r.join != nullptr);
+}
+
+Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
+  Plan p;
+  p.seg_log2 = smem_seg_log2(r);
+  p.variant = 3;
+  const bool env = std::getenv("DPG_VARIANT") || std::getenv("DPG_SEG_LOG2") || std::getenv("DPG_L2_RUN_KB");
+  if (!env && !r.join) {
+    auto it = ctx.plans.find(plan_key(r));
+    if (it != ctx.plans.end()) {
+      p.variant = it->second.first;
+      p.seg_log2 = it->second.second;
+      return p;
+    }
+  }
   p.variant = env_int("DPG_VARIANT", 3);
   const int o = env_int("DPG_SEG_LOG2", -1);
   if (o >= 0 && (1ull << o) * r.rec <= kSegBytesMax) p.seg_log2 = o;
   p.chunk = (uint32_t)env_int("DPG_CHUNK", 0);
   if (r.join) p.variant = 3;  // joins write join rows in the 3-pass Phase III
-  if (p.variant == 4) {
-    // runs of about DPG_L2_RUN_KB kilobytes of source (default 16 MB), at
-    // most kPartMaxRuns of them
-    const uint64_t want = (uint64_t)env_int("DPG_L2_RUN_KB", 16384) << 10;
-    int k = 0;
-    while (k < 31 && ((2ull << k) * r.rec) <= want) ++k;
-    while (k < 31 && ((r.n_src + (1ull << k) - 1) >> k) > kPartMaxRuns) ++k;
-    p.seg_log2 = k;
-  }
+  if (p.variant == 4) p.seg_log2 = l2_seg_log2(r, (uint64_t)env_int("DPG_L2_RUN_KB", 16384) << 10);
   return p;
+}
+
+std::vector<Plan> plan_candidates(const dpg_ctx& ctx, const Retrieval& r) {
+  (void)ctx;
+  std::vector<Plan> c;
+  const int sl = smem_seg_log2(r);
+  for (int d = 0; d <= 2; ++d)
+    if (sl - d >= 0) {
+      Plan p;
+      p.variant = 3;
+      p.seg_log2 = sl - d;
+      c.push_back(p);
+    }
+  {
+    Plan p;
+    p.variant = 2;
+    p.seg_log2 = sl;
+    c.push_back(p);
+  }
+  for (uint64_t mb : {4ull, 16ull}) {
+    Plan p;
+    p.variant = 4;
+    p.seg_log2 = l2_seg_log2(r, mb << 20);
+    if (((r.n_src + (1ull << p.seg_log2) - 1) >> p.seg_log2) <= kPartMaxRuns) c.push_back(p);
+  }
+  return c;
 }
 
 size_t retrieve_scratch_need(const dpg_ctx& ctx, const Retrieval& r) {
@@ -959,6 +1012,8 @@ size_t retrieve_scratch_need(const dpg_ctx& ctx, const Retrieval& r) {
 
 int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {
   if (r.n == 0) return DPG_OK;
+  ctx.last_variant = plan.variant;
+  ctx.last_seg_log2 = plan.seg_log2;
   if (r.n_src == 0) {
     k_flag_range<<<1, 1, 0, r.stream>>>(ctx.d_err);
     ctx.launches++;

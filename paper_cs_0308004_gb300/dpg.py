@@ -54,6 +54,8 @@ SIGNATURES = {
     "dpg_server_release": ([_P, ctypes.c_uint64], _I),
     "dpg_server_held_bytes": ([_P], _S),
     "dpg_server_destroy": ([_P], None),
+    "dpg_tune": ([_P, _P, _S, _S, _S, _P, _S, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "dpg_last_plan": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I)], None),
 }
 
 JOIN_MODES = {"move": 0, "sort": 1, "direct": 2}
@@ -281,6 +283,27 @@ class Context:
         st = lib.dpg_retrieve_batch(self._h, ctypes.cast(arr, ctypes.c_void_p), len(requests),
                                     _stream_handle(stream, self.device))
         self._check(st, "dpg_retrieve_batch")
+
+    def tune(self, src: torch.Tensor, rids: torch.Tensor, out: torch.Tensor | None = None,
+             rid_stride: int = 4, rid_off: int = 0, stream=None):
+        """Time the candidate plans on this data and cache the fastest; returns (variant, seg_log2).
+        rids: an int32 array (rid_stride 4) or uint8 key-pointer pairs (rid_stride 16, rid_off 12)."""
+        _need_cuda(src, "src", self.device)
+        _need_cuda(rids, "rids", self.device)
+        n_src, rec = _table(src, "src")
+        n = rids.shape[0]
+        if out is None:
+            out = torch.empty((n, rec), dtype=torch.uint8, device=self.device)
+        v, sl = ctypes.c_int(), ctypes.c_int()
+        st = lib.dpg_tune(self._h, src.data_ptr(), n_src, rec, n, rids.data_ptr() + rid_off, rid_stride,
+                          out.data_ptr(), _stream_handle(stream, self.device), ctypes.byref(v), ctypes.byref(sl))
+        self._check(st, "dpg_tune")
+        return v.value, sl.value
+
+    def last_plan(self):
+        v, sl = ctypes.c_int(), ctypes.c_int()
+        lib.dpg_last_plan(self._h, ctypes.byref(v), ctypes.byref(sl))
+        return v.value, sl.value
 
     # -- host buffers (copies in and out happen inside the library)
     @staticmethod

@@ -255,3 +255,27 @@ def test_sort_copy_full_size_sampled(ctx, monkeypatch, variant):
     hs = (d_src.to(torch.int64) * h).sum(1).sort().values
     ho = (out.to(torch.int64) * h).sum(1).sort().values
     assert torch.equal(hs, ho)
+
+
+@pytest.mark.parametrize("rec,stride", [(16, 4), (100, 4), (100, 16), (256, 4)])
+def test_tune_then_retrieve(rec, stride):
+    """dpg_tune caches a plan per shape; later retrievals use it and still match the oracle."""
+    from paper_cs_0308004_gb300 import dpg
+    with dpg.Context(0) as c:
+        n_src = 200_003
+        src = synth.records(n_src, rec, 3)
+        rids = synth.permutation(n_src, 4)
+        d_src = to_dev(src)
+        if stride == 4:
+            d_rids = to_dev(rids)
+            v, sl = c.tune(d_src, d_rids)
+        else:
+            pairs = np.zeros((n_src, 16), np.uint8)
+            pairs[:, 12:16] = rids.astype("<i4").view(np.uint8).reshape(-1, 4)
+            d_rids = to_dev(pairs)
+            v, sl = c.tune(d_src, d_rids, rid_stride=16, rid_off=12)
+        assert v in (2, 3, 4)
+        out = c.retrieve(d_src, to_dev(rids)) if stride == 4 else c.sort_copy(d_rids, d_src)
+        c.sync()
+        assert c.last_plan() == (v, sl)
+        assert np.array_equal(out.cpu().numpy(), oracle.retrieve(src, rids))

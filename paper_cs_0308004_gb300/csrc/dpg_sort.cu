@@ -7,36 +7,53 @@
 // strings; equal keys keep rid order.
 //
 // Phase 2 is a stable least-significant-digit radix sort with one key byte
-// per pass (byte key_bytes-1 first, byte 0 last).  Each pass: k_rs_hist counts
-// the digit of every pair per tile of kRsTile pairs (digit-major count matrix),
-// the shared scan kernels turn the counts into per-(digit, tile) cursors, and
-// k_rs_scatter ranks the tile's pairs stably (per-warp digit counts built with
-// __match_any_sync, prefix over warps), reorders the tile in shared memory and
-// writes each digit's pairs as one contiguous piece.
+// per pass (byte key_bytes-1 first, byte 0 last).  k_rs_global_hist counts
+// every key byte's digits over all pairs once (the counts do not depend on
+// the order).  Each pass is then one kernel, k_rs_onesweep: a CTA takes the
+// next tile of kRsTile pairs, ranks them stably (per-warp digit counts built
+// with __match_any_sync, prefix over warps), publishes its digit counts, and
+// finds how many pairs of each digit earlier tiles hold by looking back over
+// their published counts (decoupled look-back; every wait is bounded), then
+// reorders the tile in shared memory and writes each digit's pairs as one
+// contiguous piece at digit base + earlier tiles' count.
 #include <algorithm>
 
 #include "dpg_device.cuh"
 #include "dpg_internal.h"
-#include "dpg_scan.cuh"
 
 namespace dpg {
 namespace {
 
-constexpr int kRsThreads = 1024;
+constexpr int kRsThreads = 512;
 constexpr int kRsItems = 4;
 constexpr uint32_t kRsTile = kRsThreads * kRsItems;  // pairs per tile
 constexpr int kRsWarps = kRsThreads / 32;
 
-// Phase 1: pairs[i] = (key of record i, zero pad, i).
+// Phase 1: pairs[i] = (key of record i, zero pad, i).  WORDS: records and
+// the table are 4-byte aligned, so the key is read as ceil(key_bytes/4)
+// words (never past the record: key_bytes <= rec, rec a multiple of 4).
+template <bool WORDS>
 __global__ void __launch_bounds__(256)
     k_extract_pairs(const uint8_t* __restrict__ src, uint64_t n, uint32_t rec, uint32_t key_bytes,
                     uint4* __restrict__ pairs) {
+  const uint32_t nw = (key_bytes + 3) / 4;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint8_t* r = src + i * rec;
     uint32_t w[4] = {0u, 0u, 0u, (uint32_t)i};
+    if (WORDS) {
+      const uint32_t* rw = reinterpret_cast<const uint32_t*>(r);
 #pragma unroll
-    for (uint32_t b = 0; b < 12; ++b)
-      if (b < key_bytes) w[b >> 2] |= (uint32_t)__ldg(r + b) << (8 * (b & 3));
+      for (uint32_t j = 0; j < 3; ++j)
+        if (j < nw) {
+          const uint32_t keep = key_bytes >= 4 * (j + 1) ? 32u : 8u * (key_bytes - 4 * j);
+          const uint32_t v = __ldg(rw + j);
+          w[j] = keep == 32u ? v : (v & ((1u << keep) - 1u));
+        }
+    } else {
+#pragma unroll
+      for (uint32_t b = 0; b < 12; ++b)
+        if (b < key_bytes) w[b >> 2] |= (uint32_t)__ldg(r + b) << (8 * (b & 3));
+    }
     pairs[i] = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
@@ -46,106 +63,148 @@ __device__ __forceinline__ uint32_t pair_digit(const uint4& p, uint32_t byte) {
   return (word >> (8 * (byte & 3))) & 0xffu;
 }
 
-// Per-tile digit counts: cnt[d * ntiles + tile].
-__global__ void __launch_bounds__(kRsThreads)
-    k_rs_hist(const uint4* __restrict__ in, uint64_t n, uint32_t byte, uint32_t ntiles, uint32_t* __restrict__ cnt) {
-  __shared__ uint32_t h[256];
-  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    if (threadIdx.x < 256) h[threadIdx.x] = 0;
-    __syncthreads();
-    const uint64_t base = (uint64_t)t * kRsTile;
-#pragma unroll
-    for (int k = 0; k < kRsItems; ++k) {
-      const uint64_t e = base + (uint64_t)k * kRsThreads + threadIdx.x;
-      if (e < n) atomicAdd(&h[pair_digit(in[e], byte)], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < 256) cnt[(uint64_t)threadIdx.x * ntiles + t] = h[threadIdx.x];
-    __syncthreads();
+// Digit counts of every key byte over all pairs: counts[j * 256 + d].
+__global__ void __launch_bounds__(1024)
+    k_rs_global_hist(const uint4* __restrict__ in, uint64_t n, uint32_t key_bytes, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t h[12 * 256];
+  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x) h[x] = 0;
+  __syncthreads();
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint4 v = in[e];
+    for (uint32_t j = 0; j < key_bytes; ++j) atomicAdd(&h[j * 256 + pair_digit(v, j)], 1u);
   }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x)
+    if (h[x]) atomicAdd(&counts[x], h[x]);
 }
 
-// Stable scatter of one tile by digit.  Warp w owns tile elements
-// [128w, 128w + 128) taken in order (k major, lane minor), so the rank of an
-// element among equal digits is: its rank inside its warp step, plus the
-// equal digits of earlier steps of its warp, plus those of earlier warps.
-__global__ void __launch_bounds__(kRsThreads)
-    k_rs_scatter(const uint4* __restrict__ in, uint4* __restrict__ out, uint64_t n, uint32_t byte, uint32_t ntiles,
-                 const uint32_t* __restrict__ cur) {
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kCountMask = (1u << 30) - 1;
+
+// One stable pass on key byte `byte`.  Tiles are numbered in the order CTAs
+// start (tile_ctr), so a tile only waits for tiles whose CTAs already run.
+__global__ void __launch_bounds__(kRsThreads, 3)
+    k_rs_onesweep(const uint4* __restrict__ in, uint4* __restrict__ out, uint64_t n, uint32_t byte,
+                  const uint32_t* __restrict__ digit_count, uint32_t* status, uint32_t* tile_ctr, int* err) {
   __shared__ uint16_t whist[kRsWarps][256];
-  __shared__ uint32_t tcnt[256], toff[256];
+  __shared__ uint32_t tcnt[256], toff[256], s_base[256], s_excl[256];
+  __shared__ uint32_t s_tile;
   extern __shared__ uint4 sbuf[];                              // kRsTile pairs
   uint8_t* sdig = reinterpret_cast<uint8_t*>(sbuf + kRsTile);  // kRsTile digits
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    for (uint32_t x = threadIdx.x; x < kRsWarps * 256; x += kRsThreads) (&whist[0][0])[x] = 0;
-    __syncthreads();
-    const uint64_t base = (uint64_t)t * kRsTile;
-    uint4 v[kRsItems];
-    uint32_t d[kRsItems], rank[kRsItems];
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  for (uint32_t x = threadIdx.x; x < kRsWarps * 256; x += kRsThreads) (&whist[0][0])[x] = 0;
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint64_t base = (uint64_t)t * kRsTile;
+  // digit bases of this pass: exclusive scan of the digit counts (warp 1, 8 per lane)
+  if (warp == 1) {
+    uint32_t c[8], sum = 0;
 #pragma unroll
-    for (int k = 0; k < kRsItems; ++k) {
-      const uint64_t e = base + (uint64_t)warp * (32 * kRsItems) + (uint64_t)k * 32 + lane;
-      const bool ok = e < n;
-      if (ok) v[k] = in[e];
-      d[k] = ok ? pair_digit(v[k], byte) : 256u + lane;  // unique sentinel per lane past the end
-      const uint32_t peers = __match_any_sync(0xffffffffu, d[k]);
-      const uint32_t before = __popc(peers & lt);
-      uint32_t prior = 0;
-      if (ok) prior = whist[warp][d[k]];
-      __syncwarp();
-      if (ok && before == 0) whist[warp][d[k]] = (uint16_t)(prior + __popc(peers));
-      __syncwarp();
-      rank[k] = prior + before;
+    for (int j = 0; j < 8; ++j) {
+      c[j] = digit_count[lane * 8 + j];
+      sum += c[j];
     }
-    __syncthreads();
-    if (threadIdx.x < 256) {  // exclusive prefix over warps, per digit
-      uint32_t run = 0;
-      for (int w = 0; w < kRsWarps; ++w) {
-        const uint32_t c = whist[w][threadIdx.x];
-        whist[w][threadIdx.x] = (uint16_t)run;
-        run += c;
-      }
-      tcnt[threadIdx.x] = run;
-    }
-    __syncthreads();
-    if (warp == 0) {  // exclusive scan of the 256 digit counts, 8 per lane
-      uint32_t c[8], sum = 0;
+    uint32_t x = sum;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        c[j] = tcnt[lane * 8 + j];
-        sum += c[j];
-      }
-      uint32_t x = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      uint32_t run = x - sum;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        toff[lane * 8 + j] = run;
-        run += c[j];
-      }
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    __syncthreads();
+    uint32_t run = x - sum;
 #pragma unroll
-    for (int k = 0; k < kRsItems; ++k) {
-      if (d[k] < 256u) {
-        const uint32_t p = toff[d[k]] + whist[warp][d[k]] + rank[k];
-        sbuf[p] = v[k];
-        sdig[p] = (uint8_t)d[k];
+    for (int j = 0; j < 8; ++j) {
+      s_base[lane * 8 + j] = run;
+      run += c[j];
+    }
+  }
+  uint4 v[kRsItems];
+  uint32_t d[kRsItems], rank[kRsItems];
+#pragma unroll
+  for (int k = 0; k < kRsItems; ++k) {
+    const uint64_t e = base + (uint64_t)warp * (32 * kRsItems) + (uint64_t)k * 32 + lane;
+    const bool ok = e < n;
+    if (ok) v[k] = in[e];
+    d[k] = ok ? pair_digit(v[k], byte) : 256u + lane;  // unique sentinel per lane past the end
+    const uint32_t peers = __match_any_sync(0xffffffffu, d[k]);
+    const uint32_t before = __popc(peers & lt);
+    uint32_t prior = 0;
+    if (ok) prior = whist[warp][d[k]];
+    __syncwarp();
+    if (ok && before == 0) whist[warp][d[k]] = (uint16_t)(prior + __popc(peers));
+    __syncwarp();
+    rank[k] = prior + before;
+  }
+  __syncthreads();
+  if (threadIdx.x < 256) {  // exclusive prefix over warps, per digit
+    uint32_t run = 0;
+    for (int w = 0; w < kRsWarps; ++w) {
+      const uint32_t c = whist[w][threadIdx.x];
+      whist[w][threadIdx.x] = (uint16_t)run;
+      run += c;
+    }
+    tcnt[threadIdx.x] = run;
+    // publish this tile's count of digit d, then look back over earlier tiles
+    volatile uint32_t* st = status;
+    const uint32_t dg = threadIdx.x;
+    st[(uint64_t)t * 256 + dg] = (t == 0 ? kFlagPrefix : kFlagAgg) | run;
+    uint32_t excl = 0;
+    if (t > 0) {
+      int64_t j = (int64_t)t - 1;
+      const long long t0 = clock64();
+      while (j >= 0) {
+        const uint32_t w = st[(uint64_t)j * 256 + dg];
+        const uint32_t flag = w & ~kCountMask;
+        if (flag == 0) {
+          if (clock64() - t0 > kWaitCycles) {
+            atomicOr(err, ERR_TIMEOUT);
+            break;
+          }
+          continue;
+        }
+        excl += w & kCountMask;
+        if (flag == kFlagPrefix) break;
+        --j;
       }
+      st[(uint64_t)t * 256 + dg] = kFlagPrefix | (excl + run);
     }
-    __syncthreads();
-    const uint32_t tn = (uint32_t)((n - base) < kRsTile ? (n - base) : kRsTile);
-    for (uint32_t p = threadIdx.x; p < tn; p += kRsThreads) {
-      const uint32_t dg = sdig[p];
-      out[cur[(uint64_t)dg * ntiles + t] + (p - toff[dg])] = sbuf[p];
+    s_excl[dg] = excl;
+  }
+  __syncthreads();
+  if (warp == 0) {  // exclusive scan of the tile's 256 digit counts, 8 per lane
+    uint32_t c[8], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      c[j] = tcnt[lane * 8 + j];
+      sum += c[j];
     }
-    __syncthreads();
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    uint32_t run = x - sum;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      toff[lane * 8 + j] = run;
+      run += c[j];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kRsItems; ++k) {
+    if (d[k] < 256u) {
+      const uint32_t p = toff[d[k]] + whist[warp][d[k]] + rank[k];
+      sbuf[p] = v[k];
+      sdig[p] = (uint8_t)d[k];
+    }
+  }
+  __syncthreads();
+  const uint32_t tn = (uint32_t)((n - base) < kRsTile ? (n - base) : kRsTile);
+  for (uint32_t p = threadIdx.x; p < tn; p += kRsThreads) {
+    const uint32_t dg = sdig[p];
+    out[(uint64_t)s_base[dg] + s_excl[dg] + (p - toff[dg])] = sbuf[p];
   }
 }
 
@@ -156,7 +215,7 @@ __global__ void __launch_bounds__(kRsThreads)
 // count matrix and scan buffers (see sort_scan_bytes).
 size_t sort_scan_bytes(uint64_t n) {
   const uint64_t ntiles = (n + kRsTile - 1) / kRsTile;
-  return ((256 * ntiles * 4 + 255) & ~255ull) + 4096;
+  return ((256 * ntiles * 4 + 255) & ~255ull) + 16384;
 }
 
 uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint64_t n, uint32_t key_bytes,
@@ -165,42 +224,44 @@ uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, 
   uint4* a = reinterpret_cast<uint4*>(a_);
   uint4* b = reinterpret_cast<uint4*>(b_);
   if (n == 0) return a_;
+  if (n > kCountMask) {
+    *status = DPG_EINVAL;
+    return nullptr;
+  }
   const uint32_t ntiles = (uint32_t)((n + kRsTile - 1) / kRsTile);
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(scan);
+  uint32_t* tile_status = reinterpret_cast<uint32_t*>(scan);
   uint8_t* rest = scan + ((256ull * ntiles * 4 + 255) & ~255ull);
-  uint32_t* tot = reinterpret_cast<uint32_t*>(rest);  // 256
-  uint32_t* off = tot + 256;                            // 257
-  uint32_t* itemoff = off + 260;                        // 257
-  uint32_t* tsum = itemoff + 260;                       // 1 (+pad)
-  uint32_t* isum = tsum + 4;                            // 1 (+pad)
-  uint32_t* counter = isum + 4;
-  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)ctx.sms * 2);
+  uint32_t* counts = reinterpret_cast<uint32_t*>(rest);  // key_bytes x 256
+  uint32_t* tile_ctr = counts + 12 * 256;
+  cudaError_t e = cudaMemsetAsync(counts, 0, 12 * 256 * 4, st);
+  if (e != cudaSuccess) {
+    *status = cuda_fail(ctx, e, "memset");
+    return nullptr;
+  }
+  {
+    TraceScope ts(ctx, "k_rs_global_hist", st);
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 1023) / 1024, (uint64_t)ctx.sms * 2));
+    k_rs_global_hist<<<grid, 1024, 0, st>>>(a, n, key_bytes, counts);
+    ctx.launches++;
+  }
   const size_t smem = kRsTile * (sizeof(uint4) + 1);
-  cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_rs_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (int byte = (int)key_bytes - 1; byte >= 0; --byte) {
-    {
-      TraceScope ts(ctx, "k_rs_hist", st);
-      k_rs_hist<<<grid, kRsThreads, 0, st>>>(a, n, (uint32_t)byte, ntiles, cnt);
-    }
-    cudaError_t e = cudaMemsetAsync(tsum, 0, 32, st);
+    e = cudaMemsetAsync(tile_status, 0, (size_t)ntiles * 256 * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, 4, st);
     if (e != cudaSuccess) {
       *status = cuda_fail(ctx, e, "memset");
       return nullptr;
     }
     {
-      TraceScope ts(ctx, "k_rs_scan", st);
-      k_bucket_totals<<<256 / 32, 1024, 0, st>>>(cnt, tot, 256, ntiles, 1u << 30, tsum, isum, ctx.d_err, 1);
-      k_scan<<<256 / 32, 1024, 0, st>>>(tot, tsum, isum, 256, ntiles, 1u << 30, cnt, off, itemoff, counter,
-                                        ctx.d_err);
+      TraceScope ts(ctx, "k_rs_onesweep", st);
+      k_rs_onesweep<<<ntiles, kRsThreads, smem, st>>>(a, b, n, (uint32_t)byte, counts + 256 * byte, tile_status,
+                                                     tile_ctr, ctx.d_err);
     }
-    {
-      TraceScope ts(ctx, "k_rs_scatter", st);
-      k_rs_scatter<<<grid, kRsThreads, smem, st>>>(a, b, n, (uint32_t)byte, ntiles, cnt);
-    }
-    ctx.launches += 4;
+    ctx.launches++;
     std::swap(a, b);
   }
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) *status = cuda_fail(ctx, e, "sort launch");
   return reinterpret_cast<uint8_t*>(a);
 }
@@ -214,7 +275,10 @@ int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, 
   {
     TraceScope ts(ctx, "k_extract_pairs", st);
     const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx.sms * 8);
-    k_extract_pairs<<<grid, 256, 0, st>>>(src, n, rec, key_bytes, reinterpret_cast<uint4*>(start));
+    if (rec % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 4 == 0)
+      k_extract_pairs<true><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, reinterpret_cast<uint4*>(start));
+    else
+      k_extract_pairs<false><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, reinterpret_cast<uint4*>(start));
     ctx.launches++;
   }
   int status = DPG_OK;

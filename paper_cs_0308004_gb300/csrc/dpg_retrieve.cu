@@ -285,12 +285,17 @@ __global__ void __launch_bounds__(kProbeThreads)
         // join (§4.2.1, DPG-move): the dimension row of run entry q must carry
         // its own row number as its int64 little-endian key at pk_off
         bool bad = false;
+        const bool pk8 = (rec % 8 == 0) && (pk_off % 8 == 0);
         for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
           const uint32_t l = lo_s[q];
           const uint8_t* pr = seg + (uint64_t)l * rec + pk_off;
           uint64_t v = 0;
+          if (pk8) {
+            v = *reinterpret_cast<const uint64_t*>(pr);
+          } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) v |= (uint64_t)pr[j] << (8 * j);
+            for (int j = 0; j < 8; ++j) v |= (uint64_t)pr[j] << (8 * j);
+          }
           if (v != (((uint64_t)b << seg_log2) + l)) bad = true;
         }
         if (bad) atomicOr(err, ERR_RANGE);
@@ -510,14 +515,12 @@ struct RowField {  // int32 field of strided rows (a foreign-key column)
     return (uint64_t)(uint32_t)__ldg(reinterpret_cast<const int32_t*>(base + r * stride));
   }
 };
-struct RowPairKey {  // big-endian key bytes [0, kb) of sorted 16-byte pair r
+struct RowPairKey {  // big-endian key bytes [0, kb) of sorted 16-byte pair r (kb <= 4)
   const uint8_t* pairs;
   uint32_t kb;
   __device__ __forceinline__ uint64_t operator()(uint64_t r) const {
-    const uint8_t* p = pairs + r * 16;
-    uint64_t v = 0;
-    for (uint32_t j = 0; j < kb; ++j) v = (v << 8) | __ldg(p + j);
-    return v;
+    const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(pairs + r * 16));
+    return (uint64_t)(__byte_perm(w, 0, 0x0123) >> (8 * (4 - kb)));
   }
 };
 

@@ -658,25 +658,52 @@ def main():
 
     e2e = None
     if not a.no_e2e:
+        # End to end through the public host-buffer call (dpg_sort_copy_host):
+        # every step copies its pairs and records in from pinned host memory
+        # and its result out.  Two contexts on two host threads run
+        # alternate steps, so one step's copy-out overlaps the next one's
+        # copy-in (the copy engines run both directions at once).
+        import threading
         h_src = torch.from_numpy(src).pin_memory()
         h_pairs = torch.from_numpy(pairs).pin_memory()
-        h_out = torch.empty((n, rec), dtype=torch.uint8).pin_memory()
-        ctx.sort_copy_host(h_pairs, h_src, h_out)  # warm the context's device buffers
-        k_e2e = max(1, min(a.steps, 10))
+        lanes = 2
+        ctxs = [ctx] + [dpg.Context(local) for _ in range(lanes - 1)]
+        streams = [torch.cuda.Stream(dev) for _ in range(lanes)]
+        outs = [torch.empty((n, rec), dtype=torch.uint8).pin_memory() for _ in range(lanes)]
+        for c, st_, o in zip(ctxs, streams, outs):      # warm the contexts' device buffers
+            c.sort_copy_host(h_pairs, h_src, o, stream=st_)
+        k_e2e = max(lanes, min(a.steps, 12) // lanes * lanes)
+        errors = []
+
+        def lane(j):
+            try:
+                for _ in range(k_e2e // lanes):
+                    ctxs[j].sort_copy_host(h_pairs, h_src, outs[j], stream=streams[j])
+            except Exception as exc:  # reported below
+                errors.append(exc)
+
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(k_e2e):
-            ctx.sort_copy_host(h_pairs, h_src, h_out)
-        e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms_e2e = max_over_ranks(dist, e0.elapsed_time(e1), dev) / k_e2e
+        t0 = time.perf_counter()
+        threads = [threading.Thread(target=lane, args=(j,)) for j in range(lanes)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        torch.cuda.synchronize(dev)
+        ms_e2e = max_over_ranks(dist, (time.perf_counter() - t0) * 1e3, dev) / k_e2e
+        assert not errors, errors
         chk = np.random.default_rng(0).integers(0, n, 512)
         o = np.ascontiguousarray(pairs[:, 12:16]).view("<i4").reshape(-1)
-        assert np.array_equal(h_out.numpy()[chk], src[o[chk]])
+        for out_h in outs:
+            assert np.array_equal(out_h.numpy()[chk], src[o[chk]])
+        for c in ctxs[1:]:
+            c.close()
         e2e = {"value": round(job_gbs(world, alg_bytes, ms_e2e), 3), "unit": "GB/s",
                "ms_per_step": round(ms_e2e, 3), "h2d_bytes_per_step": n * rec + n * 16,
-               "d2h_bytes_per_step": n * rec, "api": "dpg_sort_copy_host"}
+               "d2h_bytes_per_step": n * rec, "api": "dpg_sort_copy_host",
+               "steps": k_e2e, "overlap": f"{lanes} contexts on {lanes} host threads, alternate steps",
+               "timer": "host wall clock around all steps, device synchronized at both ends"}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

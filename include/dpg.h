@@ -285,7 +285,7 @@ dpg_status dpg_trace_get(dpg_ctx* ctx, size_t index, const char** name, double* 
  *
  * Same result as dpg_retrieve (dst[i] = src[rids[i]], computed by the 2-pass
  * DPG plan), but it takes no context and allocates nothing: its scratch is a
- * fixed ~17.6 MB array that the library reserves on every device it is loaded
+ * fixed ~17.7 MB array that the library reserves on every device it is loaded
  * on, until the process exits.  Runs on the calling thread's current device;
  * all pointers are device pointers on that device.
  *   - Limits: n <= 2,097,152 rids, rec_bytes <= 65536, and at most 4096

@@ -17,7 +17,8 @@
 //                    run order, into the INTERNAL staging table (3-pass plan)
 //                    or straight into their destination slots (2-pass plan).
 //   K6 k_gather      Phase III: dst[i] = INTERNAL[slot[i]], written in rid
-//                    order as one coalesced stream.
+//                    order as one coalesced stream (k_gather16 when records
+//                    are a multiple of 4 or 8 bytes but not of 16).
 //   K1 k_gather      the baseline: dst[i] = src[rids[i]] in one pass.
 #include <algorithm>
 #include <cstdio>
@@ -85,9 +86,85 @@ __global__ void __launch_bounds__(kGatherThreads)
   if (CHECK && bad) atomicOr(err, ERR_RANGE);
 }
 
+// The same gather with the destination written as 16-byte vectors, for
+// WB = 4 or 8 (records whose size is not a multiple of 16), W >= V = 16 / WB
+// and a 16-byte-aligned destination.  Chunk c is words [V*c, V*c + V) of the
+// destination word stream; it spans at most two records and is assembled
+// from V WB-byte loads.  Two chunks per thread keep 32 bytes in flight, which
+// measured best on the Phase III slot pattern (fewer store instructions and
+// divisions than one word per thread).  The last total % V words are written
+// one by one by block 0.  With CHECK, a chunk that touches a rid outside
+// [0, n_src) writes only its words from valid records.
+constexpr int kGather16Unroll = 2;
+
+template <int WB, bool CHECK, class Idx>
+__global__ void __launch_bounds__(kGatherThreads)
+    k_gather16(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, Idx idx, uint64_t n, uint32_t W,
+               FastDiv fdW, uint32_t n_src, int* err) {
+  static_assert(WB == 4 || WB == 8, "16-byte chunks of 4- or 8-byte words");
+  using T = typename WordT<WB>::T;
+  constexpr uint32_t V = 16 / WB;
+  if (!CHECK && error_set(err)) return;
+  const T* s = reinterpret_cast<const T*>(src);
+  T* dw = reinterpret_cast<T*>(dst);
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  const uint64_t total = n * W, C = total / V;
+  const uint64_t step = (uint64_t)gridDim.x * kGatherThreads * kGather16Unroll;
+  bool bad = false;
+  for (uint64_t base = (uint64_t)blockIdx.x * kGatherThreads * kGather16Unroll + threadIdx.x; base < C;
+       base += step) {
+    T x[kGather16Unroll][V];
+    bool ok[kGather16Unroll];
+#pragma unroll
+    for (int k = 0; k < kGather16Unroll; ++k) {
+      const uint64_t c = base + (uint64_t)k * kGatherThreads;
+      ok[k] = c < C;
+      if (!ok[k]) continue;
+      const uint64_t t0 = (uint64_t)V * c;
+      const uint64_t i0 = fdiv(t0, fdW);
+      const uint32_t w0 = (uint32_t)(t0 - i0 * W);
+      const uint32_t r0 = (uint32_t)idx(i0);
+      const uint32_t r1 = (w0 + V > W) ? (uint32_t)idx(i0 + 1) : r0;
+      if (CHECK && (r0 >= n_src || r1 >= n_src)) {
+        bad = true;
+        ok[k] = false;
+#pragma unroll
+        for (uint32_t j = 0; j < V; ++j) {
+          const uint32_t w = w0 + j;
+          const uint32_t r = w < W ? r0 : r1;
+          if (r < n_src) dw[t0 + j] = s[(uint64_t)r * W + (w < W ? w : w - W)];
+        }
+        continue;
+      }
+#pragma unroll
+      for (uint32_t j = 0; j < V; ++j) {
+        const uint32_t w = w0 + j;
+        x[k][j] = w < W ? s[(uint64_t)r0 * W + w] : s[(uint64_t)r1 * W + (w - W)];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kGather16Unroll; ++k) {
+      if (!ok[k]) continue;
+      uint4 v;
+      if constexpr (WB == 4) v = make_uint4(x[k][0], x[k][1], x[k][2], x[k][3]);
+      else v = make_uint4(x[k][0].x, x[k][0].y, x[k][1].x, x[k][1].y);
+      d[base + (uint64_t)k * kGatherThreads] = v;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < total - C * V) {
+    const uint64_t t = C * V + threadIdx.x;
+    const uint64_t i = fdiv(t, fdW);
+    const uint32_t w = (uint32_t)(t - i * W);
+    const uint32_t r = (uint32_t)idx(i);
+    if (!CHECK || r < n_src) dw[t] = s[(uint64_t)r * W + w];
+    else bad = true;
+  }
+  if (CHECK && bad) atomicOr(err, ERR_RANGE);
+}
+
 // --------------------------------------------------------------------- K2
 // CTA g counts the rids of [g*per, (g+1)*per) per segment in shared memory and
-// writes its column of the bucket-major count matrix cnt[b*G + g].  With more
+// writes them as row g of the CTA-major count matrix cnt[g*nb + b].  With more
 // segments than shared counters (smem_mode == 0) it counts straight into the
 // segment totals tot[] with global atomics.
 template <class Rid>
@@ -128,7 +205,7 @@ __global__ void __launch_bounds__(kPhaseThreads)
   if (bad) atomicOr(err, ERR_RANGE);
   if (smem_mode) {
     __syncthreads();
-    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cnt[(uint64_t)b * G + g] = h[b];
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cnt[(uint64_t)g * nb + b] = h[b];
   }
 }
 
@@ -148,7 +225,7 @@ __global__ void __launch_bounds__(kPhaseThreads)
   if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
   const uint32_t g = blockIdx.x;
   if (smem_mode) {
-    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cur[b] = cur_g[(uint64_t)b * G + g];
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cur[b] = cur_g[(uint64_t)g * nb + b];
     __syncthreads();
   }
   const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
@@ -373,7 +450,7 @@ __global__ void __launch_bounds__(kPhaseThreads)
   __shared__ uint32_t s_warp[32];
   if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
   const uint32_t g = blockIdx.x;
-  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cur[b] = cur_g[(uint64_t)b * G + g];
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cur[b] = cur_g[(uint64_t)g * nb + b];
   const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint64_t t0 = lo; t0 < hi; t0 += T) {
@@ -639,10 +716,19 @@ void launch_gather(dpg_ctx& ctx, uint32_t WB, const uint8_t* src, uint8_t* dst, 
   const uint32_t W = rec / WB;
   const FastDiv f = make_fastdiv(W);
   const uint64_t total = n * W;
+  TraceScope ts(ctx, CHECK ? "k_gather_direct" : "k_gather_phase3", st);
+  if ((WB == 4 || WB == 8) && W >= 16 / WB && reinterpret_cast<uintptr_t>(dst) % 16 == 0) {
+    const uint64_t per_block = (uint64_t)kGatherThreads * kGather16Unroll;
+    const uint64_t want = (total / (16 / WB) + per_block - 1) / per_block;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx.sms * 8));
+    if (WB == 4) k_gather16<4, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err);
+    else k_gather16<8, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err);
+    ctx.launches++;
+    return;
+  }
   const uint64_t per_block = (uint64_t)kGatherThreads * kGatherUnroll;
   const uint64_t want = (total + per_block - 1) / per_block;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx.sms * 8));
-  TraceScope ts(ctx, CHECK ? "k_gather_direct" : "k_gather_phase3", st);
   switch (WB) {
     case 16: k_gather<16, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
     case 8: k_gather<8, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
@@ -690,7 +776,7 @@ struct Layout3 {
   uint32_t sl, nb, grid, G, chunk;
   uint64_t S, per;
   bool smem_mode, three, strided;
-  size_t b_cnt, b_tot, b_off, b_ctr, b_lo, b_side, b_ts, b_rc, b_stage, need;
+  size_t b_cnt, b_psum, b_tot, b_off, b_ctr, b_lo, b_side, b_ts, b_rc, b_stage, need;
 };
 
 Layout3 layout3(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, size_t lo_size, bool strided) {
@@ -707,6 +793,7 @@ Layout3 layout3(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, size_t
   L.three = plan.variant != 2 || r.join != nullptr;
   L.strided = strided;
   L.b_cnt = al((size_t)L.nb * L.G * 4);
+  L.b_psum = al((size_t)L.nb * kScanSlices * 4);
   L.b_tot = al((size_t)L.nb * 4);
   L.b_off = al(((size_t)L.nb + 1) * 4);
   L.b_ctr = 256;
@@ -715,7 +802,8 @@ Layout3 layout3(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, size_t
   L.b_ts = al((size_t)((L.nb + kScanTile - 1) / kScanTile) * 4);
   L.b_rc = strided ? al(r.n * 4) : 0;  // rids copied out of strided pairs by Phase I pass 1
   L.b_stage = L.three ? al(r.n * r.rec) : 0;
-  L.need = L.b_cnt + L.b_tot + 2 * L.b_off + L.b_ctr + 2 * L.b_ts + L.b_lo + L.b_side + L.b_rc + L.b_stage;
+  L.need = L.b_cnt + L.b_psum + L.b_tot + 2 * L.b_off + L.b_ctr + 2 * L.b_ts + L.b_lo + L.b_side + L.b_rc +
+           L.b_stage;
   return L;
 }
 
@@ -725,11 +813,12 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   const uint32_t sl = L.sl, nb = L.nb, grid = L.grid, G = L.G, chunk = L.chunk;
   const uint64_t S = L.S, per = L.per;
   const bool smem_mode = L.smem_mode, three = L.three, strided = L.strided;
-  const size_t b_cnt = L.b_cnt, b_tot = L.b_tot, b_off = L.b_off, b_ctr = L.b_ctr, b_lo = L.b_lo,
+  const size_t b_cnt = L.b_cnt, b_psum = L.b_psum, b_tot = L.b_tot, b_off = L.b_off, b_ctr = L.b_ctr, b_lo = L.b_lo,
                b_side = L.b_side, b_ts = L.b_ts, b_rc = L.b_rc;
   if (int s = ensure_scratch(ctx, L.need)) return s;
   uint8_t* p = static_cast<uint8_t*>(ctx.scratch);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(p); p += b_cnt;
+  uint32_t* psum = reinterpret_cast<uint32_t*>(p); p += b_psum;
   uint32_t* tot = reinterpret_cast<uint32_t*>(p); p += b_tot;
   uint32_t* off = reinterpret_cast<uint32_t*>(p); p += b_off;
   uint32_t* itemoff = reinterpret_cast<uint32_t*>(p); p += b_off;
@@ -755,13 +844,13 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   }
   {
     TraceScope ts(ctx, "k_bucket_totals", r.stream);
-    k_bucket_totals<<<(nb + 31) / 32, 1024, 0, r.stream>>>(cnt, tot, nb, G, chunk, tsum, isum, ctx.d_err,
-                                                           smem_mode);
+    k_bucket_totals<<<(nb + kScanBlock - 1) / kScanBlock, 1024, 0, r.stream>>>(cnt, tot, psum, nb, G, chunk,
+                                                                               tsum, isum, ctx.d_err, smem_mode);
   }
   {
     TraceScope ts(ctx, "k_scan", r.stream);
-    k_scan<<<(nb + 31) / 32, 1024, 0, r.stream>>>(tot, tsum, isum, nb, G, chunk, cnt, off, itemoff, counter,
-                                                  ctx.d_err);
+    k_scan<<<(nb + kScanBlock - 1) / kScanBlock, 1024, 0, r.stream>>>(tot, psum, tsum, isum, nb, G, chunk, cnt,
+                                                                      off, itemoff, counter, ctx.d_err, smem_mode);
   }
   ctx.launches += 2;
   {
@@ -825,8 +914,8 @@ size_t layout4_need(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bo
   const uint64_t S = 1ull << plan.seg_log2;
   const uint32_t nb = (uint32_t)((r.n_src + S - 1) >> plan.seg_log2);
   const uint32_t G = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)ctx.sms * 2, (r.n + 8191) / 8192));
-  return al((size_t)nb * G * 4) + al((size_t)nb * 4) + 2 * al(((size_t)nb + 1) * 4) + 2 * 256 +
-         2 * al((size_t)((nb + kScanTile - 1) / kScanTile) * 4) + 2 * al(r.n * 4) + (strided ? al(r.n * 4) : 0) +
+  return al((size_t)nb * G * 4) + al((size_t)nb * kScanSlices * 4) + al((size_t)nb * 4) +
+         2 * al(((size_t)nb + 1) * 4) + 2 * 256 + 2 * al((size_t)((nb + kScanTile - 1) / kScanTile) * 4) + 2 * al(r.n * 4) + (strided ? al(r.n * 4) : 0) +
          al(r.n * r.rec);
 }
 
@@ -842,13 +931,15 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   const uint32_t chunk = 1u << 30;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const bool strided = !std::is_same<Rid, RidArray>::value;
-  const size_t b_cnt = al((size_t)nb * G * 4), b_tot = al((size_t)nb * 4), b_off = al(((size_t)nb + 1) * 4);
+  const size_t b_cnt = al((size_t)nb * G * 4), b_psum = al((size_t)nb * kScanSlices * 4), b_tot = al((size_t)nb * 4),
+               b_off = al(((size_t)nb + 1) * 4);
   const size_t b_ctr = 256, b_ts = al((size_t)((nb + kScanTile - 1) / kScanTile) * 4);
   const size_t b_run = al(r.n * 4), b_slot = al(r.n * 4), b_rc = strided ? al(r.n * 4) : 0;
   const size_t need = layout4_need(ctx, r, plan, strided);
   if (int s = ensure_scratch(ctx, need)) return s;
   uint8_t* p = static_cast<uint8_t*>(ctx.scratch);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(p); p += b_cnt;
+  uint32_t* psum = reinterpret_cast<uint32_t*>(p); p += b_psum;
   uint32_t* tot = reinterpret_cast<uint32_t*>(p); p += b_tot;
   uint32_t* off = reinterpret_cast<uint32_t*>(p); p += b_off;
   uint32_t* itemoff = reinterpret_cast<uint32_t*>(p); p += b_off;
@@ -874,12 +965,13 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   }
   {
     TraceScope ts(ctx, "k_bucket_totals", r.stream);
-    k_bucket_totals<<<(nb + 31) / 32, 1024, 0, r.stream>>>(cnt, tot, nb, G, chunk, tsum, isum, ctx.d_err, 1);
+    k_bucket_totals<<<(nb + kScanBlock - 1) / kScanBlock, 1024, 0, r.stream>>>(cnt, tot, psum, nb, G, chunk,
+                                                                               tsum, isum, ctx.d_err, 1);
   }
   {
     TraceScope ts(ctx, "k_scan", r.stream);
-    k_scan<<<(nb + 31) / 32, 1024, 0, r.stream>>>(tot, tsum, isum, nb, G, chunk, cnt, off, itemoff, counter,
-                                                  ctx.d_err);
+    k_scan<<<(nb + kScanBlock - 1) / kScanBlock, 1024, 0, r.stream>>>(tot, psum, tsum, isum, nb, G, chunk, cnt,
+                                                                      off, itemoff, counter, ctx.d_err, 1);
   }
   {
     TraceScope ts(ctx, "k_partition", r.stream);
@@ -1097,7 +1189,8 @@ constexpr size_t kNaIsum = kNaTsum + 256;
 constexpr size_t kNaCnt = kNaIsum + 256;
 constexpr size_t kNaLo = kNaCnt + kNaAl((size_t)kNoallocMaxSegs * kNoallocMaxCtas * 4);
 constexpr size_t kNaDest = kNaLo + kNaAl(kNoallocMaxRids * 2);
-constexpr size_t kNoallocBytes = kNaDest + kNaAl(kNoallocMaxRids * 4);
+constexpr size_t kNaPsum = kNaDest + kNaAl(kNoallocMaxRids * 4);
+constexpr size_t kNoallocBytes = kNaPsum + kNaAl((size_t)kNoallocMaxSegs * kScanSlices * 4);
 static_assert((kNoallocMaxSegs + kScanTile - 1) / kScanTile * 4 <= 256, "tile sums fit their slot");
 
 // The scratch itself: ~17.6 MB per device.  Host code must not use this name
@@ -1187,6 +1280,7 @@ extern "C" dpg_status dpg_retrieve_noalloc(const void* src_v, size_t n_src, size
   uint32_t* cnt = reinterpret_cast<uint32_t*>(base + kNaCnt);
   uint16_t* lo = reinterpret_cast<uint16_t*>(base + kNaLo);
   uint32_t* dest = reinterpret_cast<uint32_t*>(base + kNaDest);
+  uint32_t* psum = reinterpret_cast<uint32_t*>(base + kNaPsum);
 
   // the error word and the tile sums must start at zero on every call
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
@@ -1208,8 +1302,10 @@ extern "C" dpg_status dpg_retrieve_noalloc(const void* src_v, size_t n_src, size
     set_smem(kh, phase_smem);
     kh<<<grid, kPhaseThreads, phase_smem, st>>>(rid, n, (uint32_t)n_src, sl, nb, grid, per, cnt, tot, err, 1,
                                                  nullptr);
-    k_bucket_totals<<<(nb + 31) / 32, 1024, 0, st>>>(cnt, tot, nb, grid, chunk, tsum, isum, err, 1);
-    k_scan<<<(nb + 31) / 32, 1024, 0, st>>>(tot, tsum, isum, nb, grid, chunk, cnt, off, itemoff, counter, err);
+    k_bucket_totals<<<(nb + kScanBlock - 1) / kScanBlock, 1024, 0, st>>>(cnt, tot, psum, nb, grid, chunk, tsum,
+                                                                         isum, err, 1);
+    k_scan<<<(nb + kScanBlock - 1) / kScanBlock, 1024, 0, st>>>(tot, psum, tsum, isum, nb, grid, chunk, cnt, off,
+                                                                itemoff, counter, err, 1);
     auto kd = k_distribute<RidArray, uint16_t, false>;
     set_smem(kd, phase_smem);
     kd<<<grid, kPhaseThreads, phase_smem, st>>>(rid, n, sl, nb, grid, per, cnt, lo, dest, err, 1);

@@ -57,7 +57,7 @@ def check(ctx, src, rids, variants=("dpg", "direct")):
             raise AssertionError(f"{v}: {bad.size} records differ, first at {bad[:5]}")
 
 
-RECS = [1, 2, 3, 4, 7, 8, 12, 16, 17, 32, 64, 100, 128, 255, 256, 1000, 4096]
+RECS = [1, 2, 3, 4, 7, 8, 12, 16, 17, 20, 24, 32, 40, 64, 100, 128, 255, 256, 1000, 4096]
 
 
 @pytest.mark.parametrize("variant", ["3", "2", "4"])
@@ -159,11 +159,37 @@ def test_bad_rid_leaves_destination_untouched(ctx, monkeypatch, bad, variant):
     with pytest.raises(dpg.DpgRangeError):
         ctx.sync()
     ctx.sync()  # the error was cleared
+    # the direct gather copies every record whose rid is valid
+    good = np.ones(rids.size, bool)
+    good[12345] = False
+    want = oracle.retrieve(src.cpu().numpy(), np.where(good, rids, 0))
+    assert np.array_equal(out.cpu().numpy()[good], want[good])
     # an empty source table: every rid is out of range
     empty = torch.zeros((0, rec), dtype=torch.uint8, device=DEV)
     ctx.retrieve(empty, to_dev(np.zeros(3, np.int32)))
     with pytest.raises(dpg.DpgRangeError):
         ctx.sync()
+
+
+@pytest.mark.parametrize("rec", [17, 20, 24, 100, 1000])
+def test_direct_bad_rids_copy_the_valid_records(ctx, rec):
+    """Bad rids next to each other and at the ends: every other record is
+    copied, the bad ones keep the destination's bytes (§1 baseline)."""
+    from paper_cs_0308004_gb300 import dpg
+    n_src, n = 3001, 4099
+    src = synth.records(n_src, rec, 3)
+    rids = synth.uniform_ids(n, n_src, 4)
+    bad_at = [0, 1, 2, 777, 778, 2000, n - 2, n - 1]
+    rids[bad_at] = [n_src, -5, n_src + 7, 2**31 - 1, n_src, -1, n_src, n_src]
+    out = torch.full((n, rec), 0x3C, dtype=torch.uint8, device=DEV)
+    ctx.retrieve_direct(to_dev(src), to_dev(rids), out=out)
+    with pytest.raises(dpg.DpgRangeError):
+        ctx.sync()
+    good = np.ones(n, bool)
+    good[bad_at] = False
+    got = out.cpu().numpy()
+    assert np.array_equal(got[good], oracle.retrieve(src, np.where(good, rids, 0))[good])
+    assert bool((got[~good] == 0x3C).all())
 
 
 def test_argument_errors(ctx):

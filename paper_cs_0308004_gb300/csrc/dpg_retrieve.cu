@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <type_traits>
 
@@ -40,7 +41,6 @@ constexpr int kPhaseThreads = 1024;
 constexpr int kProbeThreads = 512;
 constexpr uint32_t kSegBytesMax = 104 * 1024;  // two probe CTAs per SM (segment + staged run entries)
 constexpr uint32_t kBulkPiece = 32 * 1024;     // bytes per cp.async.bulk request
-constexpr int kDistUnroll = 4;
 constexpr int kHistUnroll = 8;
 
 // --------------------------------------------------------------- K1 / K6
@@ -425,150 +425,376 @@ __global__ void __launch_bounds__(kProbeThreads)
 
 // ------------------------------------------------------- L2-run plan (variant 4)
 // The paper sizes a run to half the cache (Figure 1, L = CACHE_SIZE/2).  On
-// GB300 the cache that many SMs share is the 126 MB L2, so this plan uses runs
-// of ~16 MB of source: Phase I partitions the rids into a few dozen runs with
-// coalesced writes, Phase II gathers each run's records in run order while the
-// run is L2-resident (the source is prefetched into L2 sequentially, one run
-// ahead), and Phase III is the same slot gather as the 3-pass plan.
+// GB300 the cache that all SMs share is the 126 MB L2, so this plan uses at most
+// kPartMaxRuns runs of a few MB of source each.
+//   Phase I  (k_part_runs): each Phase I CTA walks its rid range in tiles of T
+//            rids; a tile is counting-sorted by run in shared memory and
+//            written to the runs as contiguous pieces at the CTA's cursors.
+//            Each rid's place in its sorted tile (tpos, 2 bytes) and the
+//            tile's count per run are kept for Phase III.
+//   Phase II (k_gather over run order): INTERNAL[k] = R[run_rid[k]]; the
+//            records in flight fall in one or two runs, whose source bytes
+//            stay L2-resident while they are probed.
+//   Phase III (k_unpart_runs): the mirror of Phase I.  A tile's entries of run
+//            b form one contiguous piece of INTERNAL (at the CTA's cursor for
+//            b), so the tile reads its pieces with coalesced loads into shared
+//            memory in sorted order and writes the destination in rid order
+//            through tpos.
 
 constexpr uint32_t kPartMaxRuns = 1024;
-constexpr int kPartItems = 4;  // rids per thread per tile
+constexpr int kTileThreads = 512;
+constexpr int kTileWarps = kTileThreads / 32;
+constexpr int kPartIpt = 8;                        // Phase I tile: 4096 rids
+constexpr uint32_t kUnpartStageMax = 64 * 1024;    // Phase III shared-memory records per tile
+constexpr uint32_t kL2Ranges = 12;                 // Phase I / III CTA ranges per SM
 
-// K4': CTA g partitions the rids of [g*per, (g+1)*per) tile by tile.  Each tile
-// is counting-sorted by run in shared memory, then written to the runs as
-// contiguous pieces (run_rid[pos] = rid), and slot[i] = pos is written in rid
-// order.  The CTA's pieces of run b start at the cursor the scan reserved.
+// Exclusive scan of v[0, nb) into out[0, nb) by a block of kTileThreads
+// (nb <= 2 * kTileThreads); wsum holds 32 words of scratch.
+__device__ __forceinline__ void tile_scan(const uint32_t* v, uint32_t* out, uint32_t nb, uint32_t* wsum) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t x0 = 2 * threadIdx.x;
+  const uint32_t v0 = x0 < nb ? v[x0] : 0u, v1 = x0 + 1 < nb ? v[x0 + 1] : 0u;
+  uint32_t s = v0 + v1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= (uint32_t)o) s += y;
+  }
+  if (lane == 31) wsum[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < (uint32_t)kTileWarps ? wsum[lane] : 0u;
+    uint32_t z = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= (uint32_t)o) z += y;
+    }
+    if (lane < (uint32_t)kTileWarps) wsum[lane] = z - w;
+  }
+  __syncthreads();
+  const uint32_t e = wsum[warp] + s - v0 - v1;
+  if (x0 < nb) out[x0] = e;
+  if (x0 + 1 < nb) out[x0 + 1] = e + v0;
+  __syncthreads();
+}
+
+// Phase I, pass 1 of the L2-run plan: for each CTA range g (a block takes
+// ranges g = blockIdx.x, blockIdx.x + gridDim.x, ...) the count of its rids
+// per run, added to the run total tot[b] (zero on entry) with one atomic whose
+// old value, the range's offset inside run b, goes to cnt[g*nb + b]; the
+// range check of every rid (before any destination write); strided rids
+// copied out to `compact`.  Ranges take their places inside a run in the
+// order of the atomics; Phase I and III both read them from cnt, and the
+// result does not depend on that order.
 template <class Rid>
-__global__ void __launch_bounds__(kPhaseThreads)
-    k_partition(Rid rid, uint64_t n, uint32_t seg_log2, uint32_t nb, uint32_t G, uint64_t per,
-                const uint32_t* __restrict__ cur_g, uint32_t* __restrict__ run_rid, uint32_t* __restrict__ slot,
-                const int* err) {
-  constexpr uint32_t T = kPartItems * kPhaseThreads;
-  __shared__ uint32_t cur[kPartMaxRuns], tcnt[kPartMaxRuns], toff[kPartMaxRuns], tfill[kPartMaxRuns];
-  __shared__ uint32_t ent[T];
-  __shared__ uint16_t ent_b[T];
-  __shared__ uint32_t s_warp[32];
-  if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
-  const uint32_t g = blockIdx.x;
-  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cur[b] = cur_g[(uint64_t)g * nb + b];
-  const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint64_t t0 = lo; t0 < hi; t0 += T) {
-    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
-      tcnt[b] = 0;
-      tfill[b] = 0;
-    }
+__global__ void __launch_bounds__(kTileThreads, 4)
+    k_hist_runs(Rid rid, uint64_t n, uint32_t n_src, uint32_t sl, uint32_t nb, uint32_t G, uint64_t per,
+                uint32_t* __restrict__ cnt, uint32_t* __restrict__ tot, int* err, int32_t* __restrict__ compact) {
+  extern __shared__ uint32_t h[];
+  bool bad = false;
+  for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
+    for (uint32_t b = threadIdx.x; b < nb; b += kTileThreads) h[b] = 0;
     __syncthreads();
-    uint32_t r[kPartItems], bk[kPartItems];
+    const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
+    for (uint64_t i0 = lo + threadIdx.x; i0 < hi; i0 += (uint64_t)kHistUnroll * kTileThreads) {
+      int32_t r[kHistUnroll];
 #pragma unroll
-    for (int k = 0; k < kPartItems; ++k) {
-      const uint64_t i = t0 + (uint64_t)k * blockDim.x + threadIdx.x;
-      r[k] = i < hi ? (uint32_t)rid(i) : 0u;
-      bk[k] = r[k] >> seg_log2;
-      if (i < hi) atomicAdd(&tcnt[bk[k]], 1u);
-    }
-    __syncthreads();
-    // exclusive scan of tcnt[0, nb) (nb <= blockDim)
-    {
-      const uint32_t v = threadIdx.x < nb ? tcnt[threadIdx.x] : 0u;
-      uint32_t x = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+      for (int k = 0; k < kHistUnroll; ++k) {
+        const uint64_t i = i0 + (uint64_t)k * kTileThreads;
+        r[k] = i < hi ? rid(i) : 0;
       }
-      if (lane == 31) s_warp[warp] = x;
-      __syncthreads();
-      if (warp == 0) {
-        uint32_t w = s_warp[lane], z = w;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
-          if (lane >= o) z += y;
+      for (int k = 0; k < kHistUnroll; ++k) {
+        const uint64_t i = i0 + (uint64_t)k * kTileThreads;
+        if (i < hi) {
+          if (compact) compact[i] = r[k];
+          if ((uint32_t)r[k] >= n_src) bad = true;
+          else atomicAdd(&h[(uint32_t)r[k] >> sl], 1u);
         }
-        s_warp[lane] = z - w;
+      }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nb; b += kTileThreads)
+      cnt[(uint64_t)g * nb + b] = h[b] ? atomicAdd(&tot[b], h[b]) : 0u;
+    __syncthreads();
+  }
+  if (bad) atomicOr(err, ERR_RANGE);
+}
+
+// Exclusive scan over a block of 1024 threads; returns this thread's exclusive
+// prefix of v and sets *total (every thread) to the block sum.
+__device__ __forceinline__ uint32_t block1024_excl_scan(uint32_t v, uint32_t* wsum, uint32_t* total) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t s = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= (uint32_t)o) s += y;
+  }
+  if (lane == 31) wsum[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = wsum[lane];
+    uint32_t z = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= (uint32_t)o) z += y;
+    }
+    wsum[lane] = z - w;
+    if (lane == 31) wsum[32] = z;
+  }
+  __syncthreads();
+  const uint32_t e = wsum[warp] + s - v;
+  *total = wsum[32];
+  return e;
+}
+
+// off[b] = sum of tot[b'] for b' < b, off[nb] = n (nb <= 1024; one block).
+__global__ void __launch_bounds__(1024)
+    k_run_scan(const uint32_t* __restrict__ tot, uint32_t nb, uint32_t* __restrict__ off, const int* err) {
+  __shared__ uint32_t wsum[33];
+  if (error_set(err)) return;
+  const uint32_t v = threadIdx.x < nb ? tot[threadIdx.x] : 0u;
+  uint32_t total;
+  const uint32_t e = block1024_excl_scan(v, wsum, &total);
+  if (threadIdx.x < nb) off[threadIdx.x] = e;
+  if (threadIdx.x == 0) off[nb] = total;
+}
+
+// Phase I, pass 2 of the L2-run plan.  CTA g appends the rids of
+// [g*per, (g+1)*per) to their runs at its cursors cur_g[g*nb + b], T rids at a
+// time: the tile is counting-sorted by run in shared memory and written to the
+// runs as contiguous pieces.  For Phase III it records each rid's place in its
+// sorted tile, tpos[i] (u16), and the tile's count of each run,
+// tcnt_g[tile*nb + b] (u16), tile = i / T.
+template <int IPT>
+__global__ void __launch_bounds__(kTileThreads, 3)
+    k_part_runs(const int32_t* __restrict__ rid, uint64_t n, uint32_t sl, uint32_t nb, uint32_t G, uint64_t per,
+                const uint32_t* __restrict__ off, const uint32_t* __restrict__ cur_g, uint32_t* __restrict__ run_rid,
+                uint16_t* __restrict__ tpos, uint16_t* __restrict__ tcnt_g, const int* err) {
+  constexpr uint32_t T = kTileThreads * IPT;
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ uint32_t wsum[32];
+  if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
+  uint32_t* cur = reinterpret_cast<uint32_t*>(sm);  // run b's next position in run_rid
+  uint32_t* tcnt = cur + nb;
+  uint32_t* toff = tcnt + nb;
+  uint32_t* delta = toff + nb;                      // cur[b] - toff[b] for the tile
+  uint32_t* ent = delta + nb;
+  for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
+    for (uint32_t x = threadIdx.x; x < nb; x += kTileThreads) {
+      cur[x] = off[x] + cur_g[(uint64_t)g * nb + x];
+      tcnt[x] = 0;
+    }
+    __syncthreads();
+    const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
+    uint32_t r[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const uint64_t i = lo + k * kTileThreads + threadIdx.x;
+      r[k] = i < hi ? (uint32_t)__ldg(rid + i) : 0u;
+    }
+    for (uint64_t t0 = lo; t0 < hi; t0 += T) {
+      uint32_t rn[IPT], l[IPT];
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {  // next tile's rids, in flight meanwhile
+        const uint64_t i = t0 + T + k * kTileThreads + threadIdx.x;
+        rn[k] = i < hi ? (uint32_t)__ldg(rid + i) : 0u;
+      }
+      // count, and each rid's rank among the tile's rids of its run
+#pragma unroll
+      for (int k = 0; k < IPT; ++k)
+        if (t0 + k * kTileThreads + threadIdx.x < hi) l[k] = atomicAdd(&tcnt[r[k] >> sl], 1u);
+      __syncthreads();
+      tile_scan(tcnt, toff, nb, wsum);
+      uint16_t* tc = tcnt_g + (t0 / T) * nb;
+      for (uint32_t x = threadIdx.x; x < nb; x += kTileThreads) {
+        tc[x] = (uint16_t)tcnt[x];
+        delta[x] = cur[x] - toff[x];
+      }
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {
+        const uint64_t i = t0 + k * kTileThreads + threadIdx.x;
+        if (i < hi) {
+          const uint32_t p = toff[r[k] >> sl] + l[k];
+          ent[p] = r[k];
+          tpos[i] = (uint16_t)p;
+        }
       }
       __syncthreads();
-      if (threadIdx.x < nb) toff[threadIdx.x] = s_warp[warp] + x - v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kPartItems; ++k) {
-      const uint64_t i = t0 + (uint64_t)k * blockDim.x + threadIdx.x;
-      if (i < hi) {
-        const uint32_t p = toff[bk[k]] + atomicAdd(&tfill[bk[k]], 1u);
-        ent[p] = r[k];
-        ent_b[p] = (uint16_t)bk[k];
-        slot[i] = cur[bk[k]] + (p - toff[bk[k]]);
+      const uint32_t tn = (uint32_t)((hi - t0) < (uint64_t)T ? (hi - t0) : (uint64_t)T);
+      for (uint32_t q = threadIdx.x; q < tn; q += kTileThreads) {
+        const uint32_t rv = ent[q];
+        run_rid[delta[rv >> sl] + q] = rv;
       }
+      __syncthreads();
+      for (uint32_t x = threadIdx.x; x < nb; x += kTileThreads) {
+        cur[x] += tcnt[x];
+        tcnt[x] = 0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) r[k] = rn[k];
     }
-    __syncthreads();
-    const uint32_t tn = (uint32_t)((hi - t0) < T ? (hi - t0) : T);
-    for (uint32_t p = threadIdx.x; p < tn; p += blockDim.x) {
-      const uint32_t b = ent_b[p];
-      run_rid[cur[b] + (p - toff[b])] = ent[p];
-    }
-    __syncthreads();
-    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cur[b] += tcnt[b];
-    __syncthreads();
   }
 }
 
-// K5': INTERNAL[k] = src[run_rid[k]] in run order (the runs are consecutive
-// ranges of k).  Before each grid-stride step, thread 0 of every CTA claims
-// prefetch slices (kPfSlice bytes of source, in address order) up to the end
-// of the run after the one its next records fall in, so each run streams into
-// L2 sequentially just ahead of the random reads that probe it.
-constexpr uint32_t kPfSlice = 256 * 1024;
-
-template <int WB>
-__global__ void __launch_bounds__(kGatherThreads)
-    k_probe_l2(const uint8_t* __restrict__ src, uint8_t* __restrict__ out, const uint32_t* __restrict__ run_rid,
-               uint64_t n, uint32_t W, FastDiv fdW, const uint32_t* __restrict__ off, uint32_t nb,
-               uint64_t run_bytes, uint64_t src_bytes, uint32_t* pf_counter, int use_pf, const int* err) {
-  using T = typename WordT<WB>::T;
-  if (error_set(err)) return;
-  const T* s = reinterpret_cast<const T*>(src);
-  T* d = reinterpret_cast<T*>(out);
-  const uint64_t total = n * W;
-  const uint64_t step = (uint64_t)gridDim.x * kGatherThreads * kGatherUnroll;
-  const uint32_t n_slices = (uint32_t)((src_bytes + kPfSlice - 1) / kPfSlice);
-  for (uint64_t base = (uint64_t)blockIdx.x * kGatherThreads * kGatherUnroll + threadIdx.x; base < total;
-       base += step) {
-    if (use_pf && threadIdx.x == 0) {
-      // run of the records this CTA reaches one step from now
-      const uint64_t k_next = min(total - 1, base + step) / W;
-      uint32_t a = 0, z = nb;  // last run b with off[b] <= k_next
-      while (a < z) {
-        const uint32_t m = (a + z + 1) >> 1;
-        if (off[m] <= k_next) a = m;
-        else z = m - 1;
-      }
-      const uint64_t limit = min(src_bytes, (uint64_t)(a + 2) * run_bytes);
-      for (int claim = 0; claim < 2; ++claim) {
-        uint32_t c = *reinterpret_cast<volatile uint32_t*>(pf_counter);
-        if (c >= n_slices || (uint64_t)c * kPfSlice >= limit) break;
-        if (atomicCAS(pf_counter, c, c + 1) != c) continue;
-        const uint64_t o = (uint64_t)c * kPfSlice;
-        const uint64_t len = ((src_bytes - o) < kPfSlice ? (src_bytes - o) : kPfSlice) & ~uint64_t(15);
-        if (len) bulk_prefetch_l2(src + o, (uint32_t)len);
+// Phase III of the L2-run plan: CTA g rebuilds dst[i] for i in
+// [g*per, (g+1)*per) from INTERNAL, one Phase I tile at a time.  Run b's piece
+// of the tile is contiguous in INTERNAL (at the CTA's cursor for b) and in the
+// sorted tile (at toff[b]); a warp copies one piece at a time.  The next
+// tile's tpos and counts are loaded while the current tile is copied.
+// STAGE: pieces are copied into shared memory in sorted order (cp.async when
+// WB >= 4), then dst[t0 + j] = stage[tpos[t0 + j]] is written in rid order, as
+// 16-byte vectors when VEC (WB = 4 or 8, 16-byte-aligned destination).
+// Without STAGE (large records) each sorted entry is copied straight to its
+// destination record through the inverse of tpos.
+template <int WB, int IPT, bool STAGE, bool VEC>
+__global__ void __launch_bounds__(kTileThreads)
+    k_unpart_runs(uint64_t n, uint32_t nb, uint32_t G, uint64_t per, const uint32_t* __restrict__ off,
+                  const uint32_t* __restrict__ cur_g, const uint16_t* __restrict__ tpos,
+                  const uint16_t* __restrict__ tcnt_g, const uint8_t* __restrict__ internal,
+                  uint8_t* __restrict__ dst, uint32_t W, FastDiv fdW, const int* err) {
+  using Wd = typename WordT<WB>::T;
+  constexpr uint32_t T = kTileThreads * IPT;
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ uint32_t wsum[32];
+  if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
+  uint32_t* base = reinterpret_cast<uint32_t*>(sm);  // INTERNAL position of the tile's piece of run b
+  uint32_t* tcnt = base + nb;
+  uint32_t* toff = tcnt + nb;
+  uint16_t* pos = reinterpret_cast<uint16_t*>(sm + (((size_t)nb * 12 + 15) & ~size_t(15)));  // tpos, or its inverse
+  Wd* stage = reinterpret_cast<Wd*>(reinterpret_cast<uint8_t*>(pos) + 2 * T);
+  const Wd* iw = reinterpret_cast<const Wd*>(internal);
+  Wd* dw = reinterpret_cast<Wd*>(dst);
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // this thread owns runs x0 and x0 + 1: their cursors live in registers
+  const uint32_t x0 = 2 * threadIdx.x;
+  for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
+  uint32_t cur0 = x0 < nb ? off[x0] + cur_g[(uint64_t)g * nb + x0] : 0u;
+  uint32_t cur1 = x0 + 1 < nb ? off[x0 + 1] + cur_g[(uint64_t)g * nb + x0 + 1] : 0u;
+  const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
+  uint32_t tp[IPT], c0, c1;
+  auto fetch = [&](uint64_t t0) {
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const uint64_t i = t0 + k * kTileThreads + threadIdx.x;
+      tp[k] = i < hi ? (uint32_t)tpos[i] : 0u;
+    }
+    const uint16_t* tc = tcnt_g + (t0 / T) * nb;
+    const bool in = t0 < hi;
+    c0 = in && x0 < nb ? (uint32_t)tc[x0] : 0u;
+    c1 = in && x0 + 1 < nb ? (uint32_t)tc[x0 + 1] : 0u;
+  };
+  fetch(lo);
+  for (uint64_t t0 = lo; t0 < hi; t0 += T) {
+    const uint32_t tn = (uint32_t)((hi - t0) < (uint64_t)T ? (hi - t0) : (uint64_t)T);
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const uint32_t j = k * kTileThreads + threadIdx.x;
+      if (j < tn) {
+        if (STAGE) pos[j] = (uint16_t)tp[k];
+        else pos[tp[k]] = (uint16_t)j;
       }
     }
-    T v[kGatherUnroll];
-    bool ok[kGatherUnroll];
+    // exclusive scan of the tile's counts; cursors advance past the tile
+    {
+      uint32_t s = c0 + c1;
 #pragma unroll
-    for (int k = 0; k < kGatherUnroll; ++k) {
-      const uint64_t t = base + (uint64_t)k * kGatherThreads;
-      ok[k] = t < total;
-      if (ok[k]) {
-        const uint64_t i = fdiv(t, fdW);
-        const uint32_t w = (uint32_t)(t - i * W);
-        v[k] = s[(uint64_t)__ldg(run_rid + i) * W + w];
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= (uint32_t)o) s += y;
+      }
+      if (lane == 31) wsum[warp] = s;
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t w = lane < (uint32_t)kTileWarps ? wsum[lane] : 0u;
+        uint32_t z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+          if (lane >= (uint32_t)o) z += y;
+        }
+        if (lane < (uint32_t)kTileWarps) wsum[lane] = z - w;
+      }
+      __syncthreads();
+      const uint32_t e = wsum[warp] + s - c0 - c1;
+      if (x0 < nb) {
+        toff[x0] = e;
+        tcnt[x0] = c0;
+        base[x0] = cur0;
+        cur0 += c0;
+      }
+      if (x0 + 1 < nb) {
+        toff[x0 + 1] = e + c0;
+        tcnt[x0 + 1] = c1;
+        base[x0 + 1] = cur1;
+        cur1 += c1;
       }
     }
+    fetch(t0 + T);  // next tile, in flight meanwhile
+    __syncthreads();
+    Wd* d0 = dw + t0 * W;
+    if constexpr (STAGE) {
+      for (uint32_t b = warp; b < nb; b += kTileWarps) {
+        const uint32_t c = tcnt[b] * W;
+        const Wd* g = iw + (uint64_t)base[b] * W;
+        Wd* s = stage + toff[b] * W;
+        if constexpr (WB >= 4) {
+          for (uint32_t u = lane; u < c; u += 32) cp_async<WB>(s + u, g + u);
+        } else {
+          for (uint32_t u = lane; u < c; u += 32) s[u] = g[u];
+        }
+      }
+      if constexpr (WB >= 4) cp_async_wait_all();
+      __syncthreads();
+      const uint32_t total = tn * W;
+      if constexpr (VEC) {
+        // 16-byte chunk c = words [V*c, V*c + V) of the tile's destination
+        constexpr uint32_t V = 16 / WB;
+        const uint32_t C = total / V;
+        uint4* dv = reinterpret_cast<uint4*>(d0);
+        for (uint32_t c = threadIdx.x; c < C; c += kTileThreads) {
+          const uint32_t t = c * V;
+          uint32_t j = (uint32_t)fdiv(t, fdW), w = t - j * W;
+          Wd x[V];
 #pragma unroll
-    for (int k = 0; k < kGatherUnroll; ++k)
-      if (ok[k]) st_stream(d + base + (uint64_t)k * kGatherThreads, v[k]);
+          for (uint32_t k = 0; k < V; ++k) {
+            x[k] = stage[(uint32_t)pos[j] * W + w];
+            if (++w == W) {
+              w = 0;
+              ++j;
+            }
+          }
+          if constexpr (WB == 4) dv[c] = make_uint4(x[0], x[1], x[2], x[3]);
+          else dv[c] = make_uint4(x[0].x, x[0].y, x[1].x, x[1].y);
+        }
+        for (uint32_t t = C * V + threadIdx.x; t < total; t += kTileThreads) {
+          const uint32_t j = (uint32_t)fdiv(t, fdW), w = t - j * W;
+          d0[t] = stage[(uint32_t)pos[j] * W + w];
+        }
+      } else {
+        for (uint32_t t = threadIdx.x; t < total; t += kTileThreads) {
+          const uint32_t j = (uint32_t)fdiv(t, fdW), w = t - j * W;
+          d0[t] = stage[(uint32_t)pos[j] * W + w];
+        }
+      }
+    } else {
+      // pos[] holds the inverse: sorted entry q belongs to tile rid pos[q]
+      for (uint32_t b = warp; b < nb; b += kTileWarps) {
+        const uint32_t c = tcnt[b] * W;
+        const Wd* g = iw + (uint64_t)base[b] * W;
+        const uint32_t q0 = toff[b];
+        for (uint32_t u = lane; u < c; u += 32) {
+          const uint32_t q = (uint32_t)fdiv(u, fdW), w = u - q * W;
+          d0[(uint64_t)pos[q0 + q] * W + w] = g[u];
+        }
+      }
+    }
+    __syncthreads();
+  }
   }
 }
 
@@ -705,37 +931,67 @@ void set_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// CTAs of `kernel` resident on one SM at `threads` threads and `smem` bytes of
+// dynamic shared memory (looked up once per kernel and size).
+template <class K>
+int resident_per_sm(K kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, int> cache;
+  const std::pair<const void*, size_t> key{reinterpret_cast<const void*>(kernel), smem * 4096 + (size_t)threads};
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int nblk = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, kernel, threads, smem) != cudaSuccess || nblk < 1) {
+    cudaGetLastError();
+    nblk = 1;
+  }
+  cache[key] = nblk;
+  return nblk;
+}
+
 int env_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
   return (v && *v) ? std::atoi(v) : dflt;
 }
 
+// CTAs per SM of the grid-stride gathers: records under 64 bytes run best
+// with the SMs oversubscribed (32 CTAs per SM: 1.39 ms against 1.63 ms for one
+// resident wave at 16 bytes), larger records with exactly one resident wave
+// (0.47 against 0.56 ms at 100 bytes), measured on the 1e9-byte permutation
+// workloads; DPG_GATHER_CTAS overrides.
+template <class K>
+uint64_t gather_grid(const dpg_ctx& ctx, K kern, uint32_t rec, uint64_t want) {
+  const int knob = env_int("DPG_GATHER_CTAS", 0);
+  const int per_sm = knob > 0 ? knob : (rec < 64 ? 32 : resident_per_sm(kern, kGatherThreads, 0));
+  return std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx.sms * per_sm));
+}
+
 template <class Idx, bool CHECK>
 void launch_gather(dpg_ctx& ctx, uint32_t WB, const uint8_t* src, uint8_t* dst, Idx idx, uint64_t n, uint32_t rec,
-                   uint32_t n_src, cudaStream_t st) {
+                   uint32_t n_src, cudaStream_t st, const char* name = nullptr) {
   const uint32_t W = rec / WB;
   const FastDiv f = make_fastdiv(W);
   const uint64_t total = n * W;
-  TraceScope ts(ctx, CHECK ? "k_gather_direct" : "k_gather_phase3", st);
+  TraceScope ts(ctx, name ? name : (CHECK ? "k_gather_direct" : "k_gather_phase3"), st);
   if ((WB == 4 || WB == 8) && W >= 16 / WB && reinterpret_cast<uintptr_t>(dst) % 16 == 0) {
     const uint64_t per_block = (uint64_t)kGatherThreads * kGather16Unroll;
     const uint64_t want = (total / (16 / WB) + per_block - 1) / per_block;
-    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx.sms * 8));
-    if (WB == 4) k_gather16<4, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err);
-    else k_gather16<8, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err);
+    auto kern = WB == 4 ? k_gather16<4, CHECK, Idx> : k_gather16<8, CHECK, Idx>;
+    const int grid = (int)gather_grid(ctx, kern, rec, want);
+    kern<<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err);
     ctx.launches++;
     return;
   }
   const uint64_t per_block = (uint64_t)kGatherThreads * kGatherUnroll;
   const uint64_t want = (total + per_block - 1) / per_block;
-  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)ctx.sms * 8));
-  switch (WB) {
-    case 16: k_gather<16, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
-    case 8: k_gather<8, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
-    case 4: k_gather<4, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
-    case 2: k_gather<2, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
-    default: k_gather<1, CHECK><<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err); break;
-  }
+  auto kern = WB == 16  ? k_gather<16, CHECK, Idx>
+              : WB == 8 ? k_gather<8, CHECK, Idx>
+              : WB == 4 ? k_gather<4, CHECK, Idx>
+              : WB == 2 ? k_gather<2, CHECK, Idx>
+                        : k_gather<1, CHECK, Idx>;
+  const int grid = (int)gather_grid(ctx, kern, rec, want);
+  kern<<<grid, kGatherThreads, 0, st>>>(src, dst, idx, n, W, f, n_src, ctx.d_err);
   ctx.launches++;
 }
 
@@ -907,106 +1163,155 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
 }
 
 
-// Variant 4 (L2 runs): k_hist -> k_bucket_totals -> k_scan -> k_partition ->
-// k_probe_l2 -> k_gather_phase3.
-size_t layout4_need(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool strided) {
+// Variant 4 (L2 runs): k_hist_runs -> k_run_scan -> k_part_runs -> k_probe_l2
+// (Phase II gather in run order) -> k_unpart_runs.
+struct Layout4 {
+  uint32_t sl, nb, G, T;
+  uint64_t per, tiles;
+  bool stage_mode, strided;
+  size_t b_cnt, b_tot, b_off, b_run, b_tpos, b_tcnt, b_rc, b_stage, need;
+};
+
+// Tile of the L2-run plan (Phase I and III): the largest power of two up to
+// 4096 rids whose records fit kUnpartStageMax bytes of shared memory (at least
+// 512 rids); larger records are not staged, 2048 rids per tile.
+inline void part_tile(uint32_t rec, uint32_t& T, bool& stage) {
+  T = kTileThreads * kPartIpt;
+  while (T > (uint32_t)kTileThreads && (uint64_t)T * rec > kUnpartStageMax) T >>= 1;
+  stage = (uint64_t)T * rec <= kUnpartStageMax;
+  if (!stage) T = 2048;
+}
+
+Layout4 layout4(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool strided) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const uint64_t S = 1ull << plan.seg_log2;
-  const uint32_t nb = (uint32_t)((r.n_src + S - 1) >> plan.seg_log2);
-  const uint32_t G = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)ctx.sms * 2, (r.n + 8191) / 8192));
-  return al((size_t)nb * G * 4) + al((size_t)nb * kScanSlices * 4) + al((size_t)nb * 4) +
-         2 * al(((size_t)nb + 1) * 4) + 2 * 256 + 2 * al((size_t)((nb + kScanTile - 1) / kScanTile) * 4) + 2 * al(r.n * 4) + (strided ? al(r.n * 4) : 0) +
-         al(r.n * r.rec);
+  Layout4 L;
+  L.sl = (uint32_t)plan.seg_log2;
+  L.nb = (uint32_t)((r.n_src + (1ull << L.sl) - 1) >> L.sl);
+  part_tile(r.rec, L.T, L.stage_mode);
+  // CTA ranges: whole 4096-rid blocks (every tile starts at a multiple of T),
+  // kL2Ranges per SM so that every resident count of 2, 3 or 4 CTAs per SM
+  // takes the same number of ranges
+  const uint64_t block = (uint64_t)kTileThreads * kPartIpt;
+  const uint64_t g_max = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)ctx.sms * kL2Ranges,
+                                                                  (r.n + block - 1) / block));
+  L.per = ((r.n + g_max - 1) / g_max + block - 1) / block * block;
+  L.G = (uint32_t)((r.n + L.per - 1) / L.per);
+  L.tiles = (r.n + L.T - 1) / L.T;
+  L.strided = strided;
+  L.b_cnt = al((size_t)L.nb * L.G * 4);
+  L.b_tot = al((size_t)L.nb * 4);
+  L.b_off = al(((size_t)L.nb + 1) * 4);
+  L.b_run = al(r.n * 4);
+  L.b_tpos = al(r.n * 2);
+  L.b_tcnt = al((size_t)L.tiles * L.nb * 2);
+  L.b_rc = strided ? al(r.n * 4) : 0;
+  L.b_stage = al(r.n * r.rec);
+  L.need = L.b_cnt + L.b_tot + L.b_off + L.b_run + L.b_tpos + L.b_tcnt + L.b_rc + L.b_stage;
+  return L;
+}
+
+template <int WB, bool VEC>
+void launch_unpart(dpg_ctx& ctx, const Layout4& L, uint64_t n, uint32_t rec, const uint32_t* off,
+                   const uint32_t* cnt, const uint16_t* tpos, const uint16_t* tcnt, const uint8_t* internal,
+                   uint8_t* dst, cudaStream_t st) {
+  const uint32_t W = rec / WB;
+  const FastDiv f = make_fastdiv(W);
+  const size_t smem = (((size_t)L.nb * 12 + 15) & ~size_t(15)) + 2 * (size_t)L.T +
+                      (L.stage_mode ? (size_t)L.T * rec : 0);
+#define DPG_UNPART(IPTV, STG)                                                                                  \
+  {                                                                                                            \
+    auto kern = k_unpart_runs<WB, IPTV, STG, VEC && STG>;                                                      \
+    set_smem(kern, smem);                                                                                      \
+    const uint32_t grid = std::min<uint32_t>(L.G, ctx.sms * resident_per_sm(kern, kTileThreads, smem));        \
+    kern<<<grid, kTileThreads, smem, st>>>(n, L.nb, L.G, L.per, off, cnt, tpos, tcnt, internal, dst, W, f,     \
+                                           ctx.d_err);                                                         \
+  }
+  if (!L.stage_mode) DPG_UNPART(4, false)
+  else if (L.T == 4096) DPG_UNPART(8, true)
+  else if (L.T == 2048) DPG_UNPART(4, true)
+  else if (L.T == 1024) DPG_UNPART(2, true)
+  else DPG_UNPART(1, true)
+#undef DPG_UNPART
 }
 
 template <class Rid>
 int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
-  const uint32_t sl = (uint32_t)plan.seg_log2;
-  const uint64_t S = 1ull << sl;
-  const uint32_t nb = (uint32_t)((r.n_src + S - 1) >> sl);
-  if (nb > kPartMaxRuns) return DPG_EINVAL;
-  const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)ctx.sms * 2, (r.n + 8191) / 8192));
-  const uint32_t G = grid;
-  const uint64_t per = (r.n + grid - 1) / grid;
-  const uint32_t chunk = 1u << 30;
-  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const bool strided = !std::is_same<Rid, RidArray>::value;
-  const size_t b_cnt = al((size_t)nb * G * 4), b_psum = al((size_t)nb * kScanSlices * 4), b_tot = al((size_t)nb * 4),
-               b_off = al(((size_t)nb + 1) * 4);
-  const size_t b_ctr = 256, b_ts = al((size_t)((nb + kScanTile - 1) / kScanTile) * 4);
-  const size_t b_run = al(r.n * 4), b_slot = al(r.n * 4), b_rc = strided ? al(r.n * 4) : 0;
-  const size_t need = layout4_need(ctx, r, plan, strided);
-  if (int s = ensure_scratch(ctx, need)) return s;
+  const Layout4 L = layout4(ctx, r, plan, strided);
+  const uint32_t sl = L.sl, nb = L.nb, G = L.G;
+  if (nb > kPartMaxRuns) return DPG_EINVAL;
+  if (int s = ensure_scratch(ctx, L.need)) return s;
   uint8_t* p = static_cast<uint8_t*>(ctx.scratch);
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(p); p += b_cnt;
-  uint32_t* psum = reinterpret_cast<uint32_t*>(p); p += b_psum;
-  uint32_t* tot = reinterpret_cast<uint32_t*>(p); p += b_tot;
-  uint32_t* off = reinterpret_cast<uint32_t*>(p); p += b_off;
-  uint32_t* itemoff = reinterpret_cast<uint32_t*>(p); p += b_off;
-  uint32_t* counter = reinterpret_cast<uint32_t*>(p); p += b_ctr;
-  uint32_t* pf = reinterpret_cast<uint32_t*>(p); p += b_ctr;
-  uint32_t* tsum = reinterpret_cast<uint32_t*>(p); p += b_ts;
-  uint32_t* isum = reinterpret_cast<uint32_t*>(p); p += b_ts;
-  uint32_t* run_rid = reinterpret_cast<uint32_t*>(p); p += b_run;
-  uint32_t* slot = reinterpret_cast<uint32_t*>(p); p += b_slot;
-  int32_t* rc = strided ? reinterpret_cast<int32_t*>(p) : nullptr; p += b_rc;
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(p); p += L.b_cnt;
+  uint32_t* tot = reinterpret_cast<uint32_t*>(p); p += L.b_tot;
+  uint32_t* off = reinterpret_cast<uint32_t*>(p); p += L.b_off;
+  uint32_t* run_rid = reinterpret_cast<uint32_t*>(p); p += L.b_run;
+  uint16_t* tpos = reinterpret_cast<uint16_t*>(p); p += L.b_tpos;
+  uint16_t* tcnt = reinterpret_cast<uint16_t*>(p); p += L.b_tcnt;
+  int32_t* rc = strided ? reinterpret_cast<int32_t*>(p) : nullptr; p += L.b_rc;
   uint8_t* stage = p;
-
-  cudaError_t e = cudaMemsetAsync(tsum, 0, 2 * b_ts, r.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(pf, 0, 4, r.stream);
+  cudaError_t e = cudaMemsetAsync(tot, 0, (size_t)nb * 4, r.stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
-  const size_t phase_smem = (size_t)nb * 4;
   {
-    TraceScope ts(ctx, "k_hist", r.stream);
-    auto kern = k_hist<Rid>;
-    set_smem(kern, phase_smem);
-    kern<<<grid, kPhaseThreads, phase_smem, r.stream>>>(rid, r.n, (uint32_t)r.n_src, sl, nb, G, per, cnt, tot,
-                                                        ctx.d_err, 1, rc);
+    TraceScope ts(ctx, "k_hist_runs", r.stream);
+    const size_t smem = (size_t)nb * 4;
+    auto kern = k_hist_runs<Rid>;
+    set_smem(kern, smem);
+    const uint32_t grid = std::min<uint32_t>(G, ctx.sms * resident_per_sm(kern, kTileThreads, smem));
+    kern<<<grid, kTileThreads, smem, r.stream>>>(rid, r.n, (uint32_t)r.n_src, sl, nb, G, L.per, cnt, tot,
+                                                 ctx.d_err, rc);
   }
   {
-    TraceScope ts(ctx, "k_bucket_totals", r.stream);
-    k_bucket_totals<<<(nb + kScanBlock - 1) / kScanBlock, 1024, 0, r.stream>>>(cnt, tot, psum, nb, G, chunk,
-                                                                               tsum, isum, ctx.d_err, 1);
+    TraceScope ts(ctx, "k_run_scan", r.stream);
+    k_run_scan<<<1, 1024, 0, r.stream>>>(tot, nb, off, ctx.d_err);
   }
+  const int32_t* ra = strided ? rc : reinterpret_cast<const int32_t*>(r.rids.base);
   {
-    TraceScope ts(ctx, "k_scan", r.stream);
-    k_scan<<<(nb + kScanBlock - 1) / kScanBlock, 1024, 0, r.stream>>>(tot, psum, tsum, isum, nb, G, chunk, cnt,
-                                                                      off, itemoff, counter, ctx.d_err, 1);
+    TraceScope ts(ctx, "k_part_runs", r.stream);
+    const size_t smem = (size_t)nb * 16 + (size_t)L.T * 4;  // cur, tcnt, toff, delta, ent
+#define DPG_PART(IPTV)                                                                                          \
+  {                                                                                                             \
+    auto kern = k_part_runs<IPTV>;                                                                              \
+    set_smem(kern, smem);                                                                                       \
+    const uint32_t grid = std::min<uint32_t>(G, ctx.sms * resident_per_sm(kern, kTileThreads, smem));           \
+    kern<<<grid, kTileThreads, smem, r.stream>>>(ra, r.n, sl, nb, G, L.per, off, cnt, run_rid, tpos, tcnt,      \
+                                                 ctx.d_err);                                                    \
   }
-  {
-    TraceScope ts(ctx, "k_partition", r.stream);
-    const RidArray ra{strided ? rc : reinterpret_cast<const int32_t*>(r.rids.base)};
-    k_partition<RidArray><<<grid, kPhaseThreads, 0, r.stream>>>(ra, r.n, sl, nb, G, per, cnt, run_rid, slot,
-                                                                ctx.d_err);
+    if (L.T == 4096) DPG_PART(8)
+    else if (L.T == 2048) DPG_PART(4)
+    else if (L.T == 1024) DPG_PART(2)
+    else DPG_PART(1)
+#undef DPG_PART
   }
+  ctx.launches += 4;
+  // Phase II: INTERNAL[k] = R[run_rid[k]], k in run order
+  const uint32_t wb2 = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.src)));
+  launch_gather<SlotArray, false>(ctx, wb2, r.src, stage, SlotArray{run_rid}, r.n, r.rec, (uint32_t)r.n_src,
+                                  r.stream, "k_probe_l2");
+  // Phase III
   {
-    TraceScope ts(ctx, "k_probe_l2", r.stream);
-    const uintptr_t sa = reinterpret_cast<uintptr_t>(r.src);
-    const uint32_t wb = std::min(pow2_align(r.rec), pow2_align(sa));
-    const uint32_t W = r.rec / wb;
-    const FastDiv f = make_fastdiv(W);
-    const uint64_t total = r.n * W;
-    const uint64_t per_block = (uint64_t)kGatherThreads * kGatherUnroll;
-    // keep the records in flight (one grid step) within about DPG_L2_WINDOW_KB
-    // kilobytes (default 4 MB) so the run being probed stays L2-resident
-    const uint64_t window = (uint64_t)env_int("DPG_L2_WINDOW_KB", 4096) << 10;
-    const uint64_t by_window = std::max<uint64_t>(1, window / (per_block * wb));
-    const int pgrid = (int)std::max<uint64_t>(1, std::min<uint64_t>({(total + per_block - 1) / per_block,
-                                                                     (uint64_t)ctx.sms * 8,
-                                                                     std::max<uint64_t>(by_window, ctx.sms)}));
-    const int use_pf = (sa % 16 == 0) ? 1 : 0;
-    const uint64_t rb = S * r.rec, sb = r.n_src * r.rec;
-    switch (wb) {
-      case 16: k_probe_l2<16><<<pgrid, kGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, off, nb, rb, sb, pf, use_pf, ctx.d_err); break;
-      case 8: k_probe_l2<8><<<pgrid, kGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, off, nb, rb, sb, pf, use_pf, ctx.d_err); break;
-      case 4: k_probe_l2<4><<<pgrid, kGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, off, nb, rb, sb, pf, use_pf, ctx.d_err); break;
-      case 2: k_probe_l2<2><<<pgrid, kGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, off, nb, rb, sb, pf, use_pf, ctx.d_err); break;
-      default: k_probe_l2<1><<<pgrid, kGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, off, nb, rb, sb, pf, use_pf, ctx.d_err); break;
+    TraceScope ts(ctx, "k_unpart_runs", r.stream);
+    const uint32_t wb3 = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
+    // 16-byte destination vectors: every tile starts at a multiple of 512
+    // rids, so at a 16-byte boundary of a 16-byte-aligned destination
+    const bool vec = pow2_align(reinterpret_cast<uintptr_t>(r.dst)) == 16 && r.rec >= 16;
+#define DPG_UNP(WBV, V) launch_unpart<WBV, V>(ctx, L, r.n, r.rec, off, cnt, tpos, tcnt, stage, r.dst, r.stream)
+    switch (wb3) {
+      case 16: DPG_UNP(16, false); break;
+      case 8:
+        if (vec) DPG_UNP(8, true);
+        else DPG_UNP(8, false);
+        break;
+      case 4:
+        if (vec) DPG_UNP(4, true);
+        else DPG_UNP(4, false);
+        break;
+      case 2: DPG_UNP(2, false); break;
+      default: DPG_UNP(1, false); break;
     }
+#undef DPG_UNP
+    ctx.launches++;
   }
-  ctx.launches += 5;
-  const uint32_t wb = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
-  launch_gather<SlotArray, false>(ctx, wb, stage, r.dst, SlotArray{slot}, r.n, r.rec, (uint32_t)r.n_src, r.stream);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "dpg l2 launch");
   return DPG_OK;
@@ -1067,7 +1372,7 @@ Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
   if (o >= 0 && (1ull << o) * r.rec <= kSegBytesMax) p.seg_log2 = o;
   p.chunk = (uint32_t)env_int("DPG_CHUNK", 0);
   if (r.join) p.variant = 3;  // joins write join rows in the 3-pass Phase III
-  if (p.variant == 4) p.seg_log2 = l2_seg_log2(r, (uint64_t)env_int("DPG_L2_RUN_KB", 16384) << 10);
+  if (p.variant == 4) p.seg_log2 = l2_seg_log2(r, (uint64_t)env_int("DPG_L2_RUN_KB", 4096) << 10);
   return p;
 }
 
@@ -1088,7 +1393,7 @@ std::vector<Plan> plan_candidates(const dpg_ctx& ctx, const Retrieval& r) {
     p.seg_log2 = sl;
     c.push_back(p);
   }
-  for (uint64_t mb : {4ull, 16ull}) {
+  for (uint64_t mb : {2ull, 4ull, 8ull}) {
     Plan p;
     p.variant = 4;
     p.seg_log2 = l2_seg_log2(r, mb << 20);
@@ -1101,7 +1406,7 @@ size_t retrieve_scratch_need(const dpg_ctx& ctx, const Retrieval& r) {
   if (r.n == 0 || r.n_src == 0) return 0;
   const Plan plan = choose_plan(ctx, r);
   const bool strided = r.rids.stride != 4;
-  if (plan.variant == 4 && !r.join) return layout4_need(ctx, r, plan, strided);
+  if (plan.variant == 4 && !r.join) return layout4(ctx, r, plan, strided).need;
   return layout3(ctx, r, plan, plan.seg_log2 <= 16 ? 2 : 4, strided).need;
 }
 

@@ -73,10 +73,15 @@ const char* dpg_last_error(dpg_ctx* ctx);
  *   src       n_src records of rec_bytes bytes (the INPUT file of §2.1)
  *   rids      n int32 record ids, each in [0, n_src) (RID_LIST)
  *   dst       n records of rec_bytes bytes (OUTPUT); must not overlap src
- * Phase I partitions the rids by source segment (runs of 2^k records), Phase
- * II loads each segment into shared memory and copies its records out in
- * run order, Phase III writes the destination in rid order.  n == 0 is a no-op.
- * Duplicated and skewed rids are allowed (§2, §2.3).
+ * Phase I partitions the rids by source run (2^k consecutive records), Phase
+ * II copies each run's records out in run order while the run sits in fast
+ * memory, Phase III writes the destination in rid order.  n == 0 is a no-op.
+ * Duplicated and skewed rids are allowed (§2, §2.3).  The plan is the one
+ * dpg_tune cached for this shape, else chosen by record size: below 96 bytes
+ * runs of about 8 MB held in the L2 (tile counting sort in Phase I, tile-wise
+ * rebuild in Phase III); from 96 bytes runs of up to 104 KB held in one CTA's
+ * shared memory, with an INTERNAL staging table (3-pass) below 192 bytes and
+ * records written straight to their destination (2-pass) from 192 bytes.
  */
 dpg_status dpg_retrieve(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes,
                         size_t n, const int32_t* rids, void* dst, void* stream);
@@ -255,7 +260,7 @@ dpg_status dpg_sort_copy_host(dpg_ctx* ctx, const void* pairs, size_t pair_strid
  * size classes (log2 of n_src and n) and rid layout.  Blocking.  Candidates:
  * the 3-pass plan with shared-memory segments of the largest power-of-two
  * record count that fits 104 KB and of one half and one quarter of it, the
- * 2-pass plan, and the L2-run plan with runs of about 4 MB and 16 MB.
+ * 2-pass plan, and the L2-run plan with runs of about 4, 8 and 16 MB.
  * *variant (3, 2 or 4) and *seg_log2 receive the winner (may be NULL).
  * dpg_last_plan reports the plan of the context's last retrieval.
  */

@@ -583,56 +583,69 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   uint32_t* toff = tcnt + nb;
   uint32_t* delta = toff + nb;                      // cur[b] - toff[b] for the tile
   uint32_t* ent = delta + nb;
+  const uint32_t tid = threadIdx.x;
   for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
-    for (uint32_t x = threadIdx.x; x < nb; x += kTileThreads) {
+    for (uint32_t x = tid; x < nb; x += kTileThreads) {
       cur[x] = off[x] + cur_g[(uint64_t)g * nb + x];
       tcnt[x] = 0;
     }
     __syncthreads();
     const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
     uint32_t r[IPT];
+    {
+      const uint32_t m = (uint32_t)((hi - lo) < (uint64_t)T ? (hi - lo) : (uint64_t)T);
 #pragma unroll
-    for (int k = 0; k < IPT; ++k) {
-      const uint64_t i = lo + k * kTileThreads + threadIdx.x;
-      r[k] = i < hi ? (uint32_t)__ldg(rid + i) : 0u;
+      for (int k = 0; k < IPT; ++k) r[k] = k * kTileThreads + tid < m ? (uint32_t)__ldg(rid + lo + k * kTileThreads + tid) : 0u;
     }
     for (uint64_t t0 = lo; t0 < hi; t0 += T) {
+      const uint32_t tn = (uint32_t)((hi - t0) < (uint64_t)T ? (hi - t0) : (uint64_t)T);
+      const bool full = tn == T;
+      // next tile's rids, in flight meanwhile
       uint32_t rn[IPT], l[IPT];
+      {
+        const uint64_t t1 = t0 + T;
+        const uint32_t m = t1 < hi ? (uint32_t)((hi - t1) < (uint64_t)T ? (hi - t1) : (uint64_t)T) : 0u;
+        const int32_t* rt = rid + t1;
+        if (m == T) {
 #pragma unroll
-      for (int k = 0; k < IPT; ++k) {  // next tile's rids, in flight meanwhile
-        const uint64_t i = t0 + T + k * kTileThreads + threadIdx.x;
-        rn[k] = i < hi ? (uint32_t)__ldg(rid + i) : 0u;
+          for (int k = 0; k < IPT; ++k) rn[k] = (uint32_t)__ldg(rt + k * kTileThreads + tid);
+        } else {
+#pragma unroll
+          for (int k = 0; k < IPT; ++k) rn[k] = k * kTileThreads + tid < m ? (uint32_t)__ldg(rt + k * kTileThreads + tid) : 0u;
+        }
       }
       // count, and each rid's rank among the tile's rids of its run
 #pragma unroll
       for (int k = 0; k < IPT; ++k)
-        if (t0 + k * kTileThreads + threadIdx.x < hi) l[k] = atomicAdd(&tcnt[r[k] >> sl], 1u);
+        if (full || k * kTileThreads + tid < tn) l[k] = atomicAdd(&tcnt[r[k] >> sl], 1u);
       __syncthreads();
       tile_scan(tcnt, toff, nb, wsum);
       uint16_t* tc = tcnt_g + (t0 / T) * nb;
-      for (uint32_t x = threadIdx.x; x < nb; x += kTileThreads) {
-        tc[x] = (uint16_t)tcnt[x];
+      for (uint32_t x = tid; x < nb; x += kTileThreads) {
+        const uint32_t c = tcnt[x];
+        tc[x] = (uint16_t)c;
         delta[x] = cur[x] - toff[x];
+        cur[x] += c;
+        tcnt[x] = 0;
       }
+      uint16_t* tp = tpos + t0;
 #pragma unroll
       for (int k = 0; k < IPT; ++k) {
-        const uint64_t i = t0 + k * kTileThreads + threadIdx.x;
-        if (i < hi) {
+        const uint32_t j = k * kTileThreads + tid;
+        if (full || j < tn) {
           const uint32_t p = toff[r[k] >> sl] + l[k];
           ent[p] = r[k];
-          tpos[i] = (uint16_t)p;
+          tp[j] = (uint16_t)p;
         }
       }
       __syncthreads();
-      const uint32_t tn = (uint32_t)((hi - t0) < (uint64_t)T ? (hi - t0) : (uint64_t)T);
-      for (uint32_t q = threadIdx.x; q < tn; q += kTileThreads) {
-        const uint32_t rv = ent[q];
-        run_rid[delta[rv >> sl] + q] = rv;
-      }
-      __syncthreads();
-      for (uint32_t x = threadIdx.x; x < nb; x += kTileThreads) {
-        cur[x] += tcnt[x];
-        tcnt[x] = 0;
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {
+        const uint32_t q = k * kTileThreads + tid;
+        if (full || q < tn) {
+          const uint32_t rv = ent[q];
+          run_rid[delta[rv >> sl] + q] = rv;
+        }
       }
       __syncthreads();
 #pragma unroll
@@ -1367,12 +1380,17 @@ Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
       return p;
     }
   }
-  p.variant = env_int("DPG_VARIANT", 3);
+  // Untuned default by record size, from the 1e9-byte permutation sweep
+  // (16..64 B: L2 runs; 100 B: shared-memory segments, 3-pass; 256 B: 2-pass).
+  // Forcing a segment size or chunk keeps the shared-memory plan.
+  int dflt = r.rec < 96 ? 4 : (r.rec < 192 ? 3 : 2);
+  if (std::getenv("DPG_SEG_LOG2") || std::getenv("DPG_CHUNK")) dflt = 3;
+  p.variant = env_int("DPG_VARIANT", dflt);
   const int o = env_int("DPG_SEG_LOG2", -1);
   if (o >= 0 && (1ull << o) * r.rec <= kSegBytesMax) p.seg_log2 = o;
   p.chunk = (uint32_t)env_int("DPG_CHUNK", 0);
   if (r.join) p.variant = 3;  // joins write join rows in the 3-pass Phase III
-  if (p.variant == 4) p.seg_log2 = l2_seg_log2(r, (uint64_t)env_int("DPG_L2_RUN_KB", 4096) << 10);
+  if (p.variant == 4) p.seg_log2 = l2_seg_log2(r, (uint64_t)env_int("DPG_L2_RUN_KB", 8192) << 10);
   return p;
 }
 
@@ -1393,7 +1411,7 @@ std::vector<Plan> plan_candidates(const dpg_ctx& ctx, const Retrieval& r) {
     p.seg_log2 = sl;
     c.push_back(p);
   }
-  for (uint64_t mb : {2ull, 4ull, 8ull}) {
+  for (uint64_t mb : {4ull, 8ull, 16ull}) {
     Plan p;
     p.variant = 4;
     p.seg_log2 = l2_seg_log2(r, mb << 20);

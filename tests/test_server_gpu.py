@@ -90,8 +90,10 @@ def test_server_admission_and_errors(workload):
     from paper_cs_0308004_gb300 import dpg
     jobs, d_tables, d_dim, d_fact, wants = workload
     with dpg.Server(0, slots=2, budget_bytes=64 << 20) as srv:
-        big = to_dev(synth.permutation(200_000, 3))
-        with pytest.raises(dpg.DpgError):           # needs more than the whole budget
+        # 300,000 x 256-byte output records alone exceed the whole budget,
+        # whichever plan the retrieval takes
+        big = to_dev(synth.uniform_ids(300_000, 200_000, 3))
+        with pytest.raises(dpg.DpgError):
             srv.submit_retrieve(d_tables[256], big)
         bad = to_dev(np.array([0, 5, 200_000], np.int32))
         t = srv.submit_retrieve(d_tables[16], bad)

@@ -78,7 +78,7 @@ const char* dpg_last_error(dpg_ctx* ctx);
  * memory, Phase III writes the destination in rid order.  n == 0 is a no-op.
  * Duplicated and skewed rids are allowed (§2, §2.3).  The plan is the one
  * dpg_tune cached for this shape, else chosen by record size: below 96 bytes
- * runs of about 8 MB held in the L2 (tile counting sort in Phase I, tile-wise
+ * runs of about 16 MB held in the L2 (tile counting sort in Phase I, tile-wise
  * rebuild in Phase III); from 96 bytes runs of up to 104 KB held in one CTA's
  * shared memory, with an INTERNAL staging table (3-pass) below 192 bytes and
  * records written straight to their destination (2-pass) from 192 bytes.

@@ -95,11 +95,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Hint: bring [src, src + bytes) into L2 (16-byte aligned, multiple of 16).
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 // Asynchronous global -> shared copies of B = 4, 8 or 16 bytes (both
 // addresses B-aligned); cp_async_wait_all() waits for all of this thread's.
 template <int B> __device__ __forceinline__ void cp_async(void* smem, const void* gmem);

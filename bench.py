@@ -50,6 +50,8 @@ def args_():
     p.add_argument("--rec", type=int, default=100)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-small", action="store_true",
+                   help="skip the 16-byte-record point (62,500,000 records, permutation rids) of the line")
     p.add_argument("--sweep-recs", default="16,32,64,100,256", help="record sizes of --sweep")
     p.add_argument("--sweep-impls", default="dpg_smem,dpg_l2,dpg_tuned,direct", help="implementations of --sweep")
     p.add_argument("--join", action="store_true",
@@ -84,10 +86,10 @@ def args_():
 # variant 3), keyed by kernel; valid only while the kernel source hashes to
 # `src_sha256` (any edit of the retrieval kernels nulls the figure).
 NCU_TRAFFIC = {
-    "src_sha256": "d5bff4d170f3f6bf251ff84fd3133fe0960340f36bcd8e1771db7c63c69a06c5"
-                  ":b604ac728597a2e738ecbf5e2beaad2a21da5d72ae5f2e68163f0967070f34af",
+    "src_sha256": "9233aa1a4181b33b2bee26c08d4c52fdd2acb11f005637f4c4e01cdacb8d385b"
+                  ":5eccae304881b1c2197a96b3d20def24e4f4fdac52f01beaf026764ec77fd6c2",
     "n": 10_000_000, "rec": 100,
-    "bytes": {"k_probe": 1020107776 + 944108288, "k_gather_phase3": 1040067584 + 955951616},
+    "bytes": {"k_probe": 1020184832 + 946568448, "k_gather_phase3": 1040505344 + 955376384},
 }
 
 
@@ -653,6 +655,32 @@ def main():
     ms_sortall, _, _ = timed(lambda: ctx.sort_records(d_src, 10, out=d_out))
     del g_pairs
 
+    # The same retrieval at 16-byte records (the record-size sweep's smallest
+    # size, 1e9 bytes of source, rids a permutation): where the paper finds
+    # DPG gains most.  Reported beside the headline, not in it.
+    small = None
+    if not a.no_small:
+        rs = 16
+        ns = 10 ** 9 // rs
+        s_src = torch.from_numpy(synth.records(ns, rs, 3)).to(dev)
+        s_rids = torch.from_numpy(synth.permutation(ns, 2)).to(dev)
+        s_out = torch.empty((ns, rs), dtype=torch.uint8, device=dev)
+        s_plan = ctx.tune(s_src, s_rids, s_out)
+        ms_s, _, _ = timed(lambda: ctx.retrieve(s_src, s_rids, out=s_out))
+        chk = torch.randint(0, ns, (4096,), device=dev)
+        assert torch.equal(s_out[chk], s_src[s_rids[chk].long()]), "16-byte DPG output differs from src[rid]"
+        ms_sd, _, _ = timed(lambda: ctx.retrieve_direct(s_src, s_rids, out=s_out))
+        sb = ns * (2 * rs + 4)
+        small = {"workload": f"{ns:,} x {rs}-byte records (1e9 B, seed 3), rids a permutation (seed 2)",
+                 "algorithmic_bytes_per_step": sb,
+                 "dpg": {"value": round(job_gbs(world, sb, ms_s), 3), "unit": "GB/s", "ms_per_step": round(ms_s, 4),
+                         "plan": {"variant": s_plan[0], "seg_log2": s_plan[1]}},
+                 "direct_gather": {"value": round(job_gbs(world, sb, ms_sd), 3), "unit": "GB/s",
+                                   "ms_per_step": round(ms_sd, 4)},
+                 "speedup_vs_direct": round(ms_sd / ms_s, 4)}
+        del s_src, s_rids, s_out
+        torch.cuda.empty_cache()
+
     # per-kernel CUDA-event durations on the launching stream
     ctx.trace_reset()
     ctx.trace(True)
@@ -751,6 +779,7 @@ def main():
             "direct_gather": {"value": round(direct, 3), "unit": "GB/s", "ms_per_step": round(ms_dir, 4),
                               "pct_of_hbm_peak": round(direct / world / peak, 4)},
             "speedup_vs_direct": round(ms_dir / ms_dpg, 4),
+            "small_records": small,
             "full_sort": {"ms_per_sort": round(ms_sortall, 4), "keyptr_sort_ms": round(ms_keyptr, 4),
                           "records_per_s": round(world * n / (ms_sortall * 1e-3), 1),
                           "what": "dpg_sort_records: extract pairs + stable 10-pass LSD radix sort + DPG copy"},

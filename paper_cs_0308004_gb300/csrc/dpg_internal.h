@@ -106,6 +106,7 @@ struct Retrieval {
 // Limits of the DPG path.
 constexpr uint32_t kMaxDpgRecBytes = 65536;   // a segment holds at least one record
 constexpr uint32_t kSmemBuckets = 24576;      // Phase I per-CTA counters fit in 96 KB
+constexpr uint32_t kL2MaxRuns = 1024;         // runs of the L2-run plan (variant 4)
 
 // Plan chosen for a retrieval: environment overrides (DPG_VARIANT,
 // DPG_SEG_LOG2, DPG_CHUNK, DPG_L2_RUN_KB) when set, else a plan dpg_tune
@@ -121,6 +122,15 @@ size_t retrieve_scratch_need(const dpg_ctx& ctx, const Retrieval& r);
 // Enqueue the DPG retrieval / the direct gather.  Return a dpg_status.
 int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan);
 int run_direct(dpg_ctx& ctx, const Retrieval& r);
+
+// The L2-run plan (variant 4, dpg_runs.cu) and its scratch bytes.
+int run_dpg_l2(dpg_ctx& ctx, const Retrieval& r, const Plan& plan);
+size_t l2_scratch_need(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool strided);
+
+// dst[k] = src[slot[k]] for k in [0, n) by the grid-stride gather, in words of
+// wb bytes (dpg_retrieve.cu); `name` labels the launch in traces.
+void launch_slot_gather(dpg_ctx& ctx, uint32_t wb, const uint8_t* src, uint8_t* dst, const uint32_t* slot,
+                        uint64_t n, uint32_t rec, uint32_t n_src, cudaStream_t st, const char* name);
 
 // Scratch arena helpers (dpg_api.cu).
 int ensure_scratch(dpg_ctx& ctx, size_t bytes);

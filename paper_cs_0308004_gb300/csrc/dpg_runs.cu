@@ -1,0 +1,710 @@
+// DPG record retrieval with runs held in the L2 (plan variant 4): Phase I
+// partitions the rids into at most kL2MaxRuns runs of a few MB of source,
+// Phase II probes each run while its source bytes are L2-resident, Phase III
+// rebuilds the destination tile by tile (§2.1, Figure 1; run length: §2.1's
+// L = half the cache, here the GPU's shared L2).
+#include <algorithm>
+#include <cstdio>
+#include <type_traits>
+
+#include "dpg_device.cuh"
+#include "dpg_internal.h"
+#include "dpg_launch.cuh"
+
+namespace dpg {
+namespace {
+
+constexpr int kRunsHistUnroll = 8;
+constexpr int kRunsGatherThreads = 256;
+constexpr int kRunsGatherUnroll = 8;
+
+// ------------------------------------------------------- L2-run plan (variant 4)
+// The paper sizes a run to half the cache (Figure 1, L = CACHE_SIZE/2).  On
+// GB300 the cache that all SMs share is the 126 MB L2, so this plan uses at most
+// kL2MaxRuns runs of a few MB of source each.
+//   Phase I  (k_part_runs): each Phase I CTA walks its rid range in tiles of T
+//            rids; a tile is counting-sorted by run in shared memory and
+//            written to the runs as contiguous pieces at the CTA's cursors.
+//            Each rid's place in its sorted tile (tpos, 2 bytes) and the
+//            tile's count per run are kept for Phase III.
+//   Phase II (k_gather over run order): INTERNAL[k] = R[run_rid[k]]; the
+//            records in flight fall in one or two runs, whose source bytes
+//            stay L2-resident while they are probed.
+//   Phase III (k_unpart_runs): the mirror of Phase I.  A tile's entries of run
+//            b form one contiguous piece of INTERNAL (at the CTA's cursor for
+//            b), so the tile reads its pieces with coalesced loads into shared
+//            memory in sorted order and writes the destination in rid order
+//            through tpos.
+
+constexpr int kTileThreads = 512;
+constexpr int kTileWarps = kTileThreads / 32;
+constexpr int kPartIpt = 8;                        // Phase I tile: 4096 rids
+constexpr uint32_t kUnpartStageMax = 64 * 1024;    // Phase III shared-memory records per tile
+constexpr uint32_t kL2Ranges = 12;                 // Phase I / III CTA ranges per SM
+
+// Exclusive scan of v[0, nb) into out[0, nb) by a block of kTileThreads
+// (nb <= 2 * kTileThreads); wsum holds 32 words of scratch.
+__device__ __forceinline__ void tile_scan(const uint32_t* v, uint32_t* out, uint32_t nb, uint32_t* wsum) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t x0 = 2 * threadIdx.x;
+  const uint32_t v0 = x0 < nb ? v[x0] : 0u, v1 = x0 + 1 < nb ? v[x0 + 1] : 0u;
+  uint32_t s = v0 + v1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= (uint32_t)o) s += y;
+  }
+  if (lane == 31) wsum[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < (uint32_t)kTileWarps ? wsum[lane] : 0u;
+    uint32_t z = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= (uint32_t)o) z += y;
+    }
+    if (lane < (uint32_t)kTileWarps) wsum[lane] = z - w;
+  }
+  __syncthreads();
+  const uint32_t e = wsum[warp] + s - v0 - v1;
+  if (x0 < nb) out[x0] = e;
+  if (x0 + 1 < nb) out[x0 + 1] = e + v0;
+  __syncthreads();
+}
+
+// Phase I, pass 1 of the L2-run plan: for each CTA range g (a block takes
+// ranges g = blockIdx.x, blockIdx.x + gridDim.x, ...) the count of its rids
+// per run, added to the run total tot[b] (zero on entry) with one atomic whose
+// old value, the range's offset inside run b, goes to cnt[g*nb + b]; the
+// range check of every rid (before any destination write); strided rids
+// copied out to `compact`.  Ranges take their places inside a run in the
+// order of the atomics; Phase I and III both read them from cnt, and the
+// result does not depend on that order.
+template <class Rid>
+__global__ void __launch_bounds__(kTileThreads, 4)
+    k_hist_runs(Rid rid, uint64_t n, uint32_t n_src, uint32_t sl, uint32_t nb, uint32_t G, uint64_t per,
+                uint32_t* __restrict__ cnt, uint32_t* __restrict__ tot, int* err, int32_t* __restrict__ compact) {
+  extern __shared__ uint32_t h[];
+  bool bad = false;
+  for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
+    for (uint32_t b = threadIdx.x; b < nb; b += kTileThreads) h[b] = 0;
+    __syncthreads();
+    const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
+    for (uint64_t i0 = lo + threadIdx.x; i0 < hi; i0 += (uint64_t)kRunsHistUnroll * kTileThreads) {
+      int32_t r[kRunsHistUnroll];
+#pragma unroll
+      for (int k = 0; k < kRunsHistUnroll; ++k) {
+        const uint64_t i = i0 + (uint64_t)k * kTileThreads;
+        r[k] = i < hi ? rid(i) : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kRunsHistUnroll; ++k) {
+        const uint64_t i = i0 + (uint64_t)k * kTileThreads;
+        if (i < hi) {
+          if (compact) compact[i] = r[k];
+          if ((uint32_t)r[k] >= n_src) bad = true;
+          else atomicAdd(&h[(uint32_t)r[k] >> sl], 1u);
+        }
+      }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nb; b += kTileThreads)
+      cnt[(uint64_t)g * nb + b] = h[b] ? atomicAdd(&tot[b], h[b]) : 0u;
+    __syncthreads();
+  }
+  if (bad) atomicOr(err, ERR_RANGE);
+}
+
+// The same for an int32 rid array at a 16-byte-aligned address (no copy-out):
+// the rids are read as 16-byte vectors of four (CTA ranges start at multiples
+// of 4096 rids, so every range starts 16-byte aligned).
+__global__ void __launch_bounds__(kTileThreads, 4)
+    k_hist_runs4(const int32_t* __restrict__ rid, uint64_t n, uint32_t n_src, uint32_t sl, uint32_t nb, uint32_t G,
+                 uint64_t per, uint32_t* __restrict__ cnt, uint32_t* __restrict__ tot, int* err) {
+  extern __shared__ uint32_t h[];
+  bool bad = false;
+  auto count = [&](int32_t x) {
+    if ((uint32_t)x >= n_src) bad = true;
+    else atomicAdd(&h[(uint32_t)x >> sl], 1u);
+  };
+  for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
+    for (uint32_t b = threadIdx.x; b < nb; b += kTileThreads) h[b] = 0;
+    __syncthreads();
+    const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
+    const int4* r4 = reinterpret_cast<const int4*>(rid + lo);
+    const uint32_t nv = (uint32_t)((hi - lo) >> 2);
+    for (uint32_t v = threadIdx.x; v < nv; v += 2 * kTileThreads) {
+      const int4 a = __ldg(r4 + v);
+      const bool two = v + kTileThreads < nv;
+      const int4 c = two ? __ldg(r4 + v + kTileThreads) : make_int4(0, 0, 0, 0);
+      count(a.x);
+      count(a.y);
+      count(a.z);
+      count(a.w);
+      if (two) {
+        count(c.x);
+        count(c.y);
+        count(c.z);
+        count(c.w);
+      }
+    }
+    for (uint64_t i = lo + 4 * (uint64_t)nv + threadIdx.x; i < hi; i += kTileThreads) count(__ldg(rid + i));
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nb; b += kTileThreads)
+      cnt[(uint64_t)g * nb + b] = h[b] ? atomicAdd(&tot[b], h[b]) : 0u;
+    __syncthreads();
+  }
+  if (bad) atomicOr(err, ERR_RANGE);
+}
+
+// Exclusive scan over a block of 1024 threads; returns this thread's exclusive
+// prefix of v and sets *total (every thread) to the block sum.
+__device__ __forceinline__ uint32_t block1024_excl_scan(uint32_t v, uint32_t* wsum, uint32_t* total) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t s = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+    if (lane >= (uint32_t)o) s += y;
+  }
+  if (lane == 31) wsum[warp] = s;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = wsum[lane];
+    uint32_t z = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= (uint32_t)o) z += y;
+    }
+    wsum[lane] = z - w;
+    if (lane == 31) wsum[32] = z;
+  }
+  __syncthreads();
+  const uint32_t e = wsum[warp] + s - v;
+  *total = wsum[32];
+  return e;
+}
+
+// off[b] = sum of tot[b'] for b' < b, off[nb] = n (nb <= 1024; one block).
+__global__ void __launch_bounds__(1024)
+    k_run_scan(const uint32_t* __restrict__ tot, uint32_t nb, uint32_t* __restrict__ off, const int* err) {
+  __shared__ uint32_t wsum[33];
+  if (error_set(err)) return;
+  const uint32_t v = threadIdx.x < nb ? tot[threadIdx.x] : 0u;
+  uint32_t total;
+  const uint32_t e = block1024_excl_scan(v, wsum, &total);
+  if (threadIdx.x < nb) off[threadIdx.x] = e;
+  if (threadIdx.x == 0) off[nb] = total;
+}
+
+// Phase I, pass 2 of the L2-run plan.  CTA g appends the rids of
+// [g*per, (g+1)*per) to their runs at its cursors cur_g[g*nb + b], T rids at a
+// time: the tile is counting-sorted by run in shared memory and written to the
+// runs as contiguous pieces.  For Phase III it records each rid's place in its
+// sorted tile, tpos[i] (u16), and the tile's count of each run,
+// tcnt_g[tile*nb + b] (u16), tile = i / T.
+template <int IPT>
+__global__ void __launch_bounds__(kTileThreads, 3)
+    k_part_runs(const int32_t* __restrict__ rid, uint64_t n, uint32_t sl, uint32_t nb, uint32_t G, uint64_t per,
+                const uint32_t* __restrict__ off, const uint32_t* __restrict__ cur_g, uint32_t* __restrict__ run_rid,
+                uint16_t* __restrict__ tpos, uint16_t* __restrict__ tcnt_g, const int* err) {
+  constexpr uint32_t T = kTileThreads * IPT;
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ uint32_t wsum[32];
+  if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
+  uint32_t* cur = reinterpret_cast<uint32_t*>(sm);  // run b's next position in run_rid
+  uint32_t* tcnt = cur + nb;
+  uint32_t* toff = tcnt + nb;
+  uint32_t* delta = toff + nb;                      // cur[b] - toff[b] for the tile
+  uint32_t* ent = delta + nb;
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
+    for (uint32_t x = tid; x < nb; x += kTileThreads) {
+      cur[x] = off[x] + cur_g[(uint64_t)g * nb + x];
+      tcnt[x] = 0;
+    }
+    __syncthreads();
+    const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
+    uint32_t r[IPT];
+    {
+      const uint32_t m = (uint32_t)((hi - lo) < (uint64_t)T ? (hi - lo) : (uint64_t)T);
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) r[k] = k * kTileThreads + tid < m ? (uint32_t)__ldg(rid + lo + k * kTileThreads + tid) : 0u;
+    }
+    for (uint64_t t0 = lo; t0 < hi; t0 += T) {
+      const uint32_t tn = (uint32_t)((hi - t0) < (uint64_t)T ? (hi - t0) : (uint64_t)T);
+      const bool full = tn == T;
+      // next tile's rids, in flight meanwhile
+      uint32_t rn[IPT], l[IPT];
+      {
+        const uint64_t t1 = t0 + T;
+        const uint32_t m = t1 < hi ? (uint32_t)((hi - t1) < (uint64_t)T ? (hi - t1) : (uint64_t)T) : 0u;
+        const int32_t* rt = rid + t1;
+        if (m == T) {
+#pragma unroll
+          for (int k = 0; k < IPT; ++k) rn[k] = (uint32_t)__ldg(rt + k * kTileThreads + tid);
+        } else {
+#pragma unroll
+          for (int k = 0; k < IPT; ++k) rn[k] = k * kTileThreads + tid < m ? (uint32_t)__ldg(rt + k * kTileThreads + tid) : 0u;
+        }
+      }
+      // count, and each rid's rank among the tile's rids of its run
+#pragma unroll
+      for (int k = 0; k < IPT; ++k)
+        if (full || k * kTileThreads + tid < tn) l[k] = atomicAdd(&tcnt[r[k] >> sl], 1u);
+      __syncthreads();
+      tile_scan(tcnt, toff, nb, wsum);
+      uint16_t* tc = tcnt_g + (t0 / T) * nb;
+      for (uint32_t x = tid; x < nb; x += kTileThreads) {
+        const uint32_t c = tcnt[x];
+        tc[x] = (uint16_t)c;
+        delta[x] = cur[x] - toff[x];
+        cur[x] += c;
+        tcnt[x] = 0;
+      }
+      uint16_t* tp = tpos + t0;
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {
+        const uint32_t j = k * kTileThreads + tid;
+        if (full || j < tn) {
+          const uint32_t p = toff[r[k] >> sl] + l[k];
+          ent[p] = r[k];
+          tp[j] = (uint16_t)p;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) {
+        const uint32_t q = k * kTileThreads + tid;
+        if (full || q < tn) {
+          const uint32_t rv = ent[q];
+          run_rid[delta[rv >> sl] + q] = rv;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < IPT; ++k) r[k] = rn[k];
+    }
+  }
+}
+
+// Phase II of the L2-run plan for records under 64 bytes: INTERNAL[k] =
+// R[run_rid[k]] for k in run order.  One resident wave of CTAs claims chunks
+// of kRunsGatherThreads * U words in increasing k from *ctr, so the records
+// probed at any time lie in one or two runs, which stay L2-resident.  The next
+// chunk is claimed, and its rids loaded, while this chunk's source reads are
+// in flight (one dependent round trip per chunk instead of two).
+// (Larger records use the grid-stride gather over run order; having the L2
+// prefetch the next run with cp.async.bulk.prefetch was measured slower:
+// 590 against 442 us at 16 bytes.)
+template <int WB>
+__global__ void __launch_bounds__(kRunsGatherThreads, 4)
+    k_probe_runs(const uint8_t* __restrict__ src, uint8_t* __restrict__ out, const uint32_t* __restrict__ run_rid,
+                 uint64_t n, uint32_t W, FastDiv fdW, unsigned long long* ctr, const int* err) {
+  using T = typename WordT<WB>::T;
+  constexpr int U = WB == 16 ? 4 : kRunsGatherUnroll;  // words per thread per chunk (64 B of 16-byte words)
+  constexpr uint32_t CH = kRunsGatherThreads * U;
+  __shared__ uint64_t s_c[2];
+  if (error_set(err)) return;
+  const T* s = reinterpret_cast<const T*>(src);
+  T* d = reinterpret_cast<T*>(out);
+  const uint64_t total = n * W;
+  const uint64_t nch = (total + CH - 1) / CH;
+  // rid of each of this thread's words of chunk c
+  auto load_ids = [&](uint64_t c, uint32_t (&id)[U]) {
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const uint64_t t = c * CH + (uint64_t)k * kRunsGatherThreads + threadIdx.x;
+      id[k] = (c < nch && t < total) ? __ldg(run_rid + fdiv(t, fdW)) : 0u;
+    }
+  };
+  if (threadIdx.x == 0) s_c[0] = atomicAdd(ctr, 1ull);
+  __syncthreads();
+  uint64_t c = s_c[0];
+  uint32_t id[U];
+  load_ids(c, id);
+  // The next chunk is claimed and its rids loaded while this chunk's source
+  // reads are in flight.
+  for (int buf = 1; c < nch; buf ^= 1) {
+    if (threadIdx.x == 0) s_c[buf] = atomicAdd(ctr, 1ull);
+    const uint64_t base = c * CH + threadIdx.x;
+    T v[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const uint64_t t = base + (uint64_t)k * kRunsGatherThreads;
+      if (t < total) {
+        const uint32_t w = (uint32_t)(t - fdiv(t, fdW) * W);
+        v[k] = s[(uint64_t)id[k] * W + w];
+      }
+    }
+    __syncthreads();
+    const uint64_t cn = s_c[buf];
+    load_ids(cn, id);
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const uint64_t t = base + (uint64_t)k * kRunsGatherThreads;
+      if (t < total) d[t] = v[k];
+    }
+    c = cn;
+  }
+}
+
+// Phase III of the L2-run plan: CTA g rebuilds dst[i] for i in
+// [g*per, (g+1)*per) from INTERNAL, one Phase I tile at a time.  Run b's piece
+// of the tile is contiguous in INTERNAL (at the CTA's cursor for b) and in the
+// sorted tile (at toff[b]); a warp copies one piece at a time.  The next
+// tile's tpos and counts are loaded while the current tile is copied.
+// STAGE: pieces are copied into shared memory in sorted order (cp.async when
+// WB >= 4), then dst[t0 + j] = stage[tpos[t0 + j]] is written in rid order, as
+// 16-byte vectors when VEC (WB = 4 or 8, 16-byte-aligned destination).
+// Without STAGE (large records) each sorted entry is copied straight to its
+// destination record through the inverse of tpos.
+template <int WB, int IPT, bool STAGE, bool VEC>
+__global__ void __launch_bounds__(kTileThreads)
+    k_unpart_runs(uint64_t n, uint32_t nb, uint32_t G, uint64_t per, const uint32_t* __restrict__ off,
+                  const uint32_t* __restrict__ cur_g, const uint16_t* __restrict__ tpos,
+                  const uint16_t* __restrict__ tcnt_g, const uint8_t* __restrict__ internal,
+                  uint8_t* __restrict__ dst, uint32_t W, FastDiv fdW, const int* err) {
+  using Wd = typename WordT<WB>::T;
+  constexpr uint32_t T = kTileThreads * IPT;
+  extern __shared__ __align__(16) uint8_t sm[];
+  __shared__ uint32_t wsum[32];
+  if (__syncthreads_or(threadIdx.x == 0 && error_set(err))) return;
+  uint32_t* base = reinterpret_cast<uint32_t*>(sm);  // INTERNAL position of the tile's piece of run b
+  uint32_t* tcnt = base + nb;
+  uint32_t* toff = tcnt + nb;
+  uint16_t* pos = reinterpret_cast<uint16_t*>(sm + (((size_t)nb * 12 + 15) & ~size_t(15)));  // tpos, or its inverse
+  Wd* stage = reinterpret_cast<Wd*>(reinterpret_cast<uint8_t*>(pos) + 2 * T);
+  const Wd* iw = reinterpret_cast<const Wd*>(internal);
+  Wd* dw = reinterpret_cast<Wd*>(dst);
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // this thread owns runs x0 and x0 + 1: their cursors live in registers
+  const uint32_t x0 = 2 * threadIdx.x;
+  for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
+  uint32_t cur0 = x0 < nb ? off[x0] + cur_g[(uint64_t)g * nb + x0] : 0u;
+  uint32_t cur1 = x0 + 1 < nb ? off[x0 + 1] + cur_g[(uint64_t)g * nb + x0 + 1] : 0u;
+  const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
+  uint32_t tp[IPT], c0, c1;
+  auto fetch = [&](uint64_t t0) {
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const uint64_t i = t0 + k * kTileThreads + threadIdx.x;
+      tp[k] = i < hi ? (uint32_t)tpos[i] : 0u;
+    }
+    const uint16_t* tc = tcnt_g + (t0 / T) * nb;
+    const bool in = t0 < hi;
+    c0 = in && x0 < nb ? (uint32_t)tc[x0] : 0u;
+    c1 = in && x0 + 1 < nb ? (uint32_t)tc[x0 + 1] : 0u;
+  };
+  fetch(lo);
+  for (uint64_t t0 = lo; t0 < hi; t0 += T) {
+    const uint32_t tn = (uint32_t)((hi - t0) < (uint64_t)T ? (hi - t0) : (uint64_t)T);
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const uint32_t j = k * kTileThreads + threadIdx.x;
+      if (j < tn) {
+        if (STAGE) pos[j] = (uint16_t)tp[k];
+        else pos[tp[k]] = (uint16_t)j;
+      }
+    }
+    // exclusive scan of the tile's counts; cursors advance past the tile
+    {
+      uint32_t s = c0 + c1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= (uint32_t)o) s += y;
+      }
+      if (lane == 31) wsum[warp] = s;
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t w = lane < (uint32_t)kTileWarps ? wsum[lane] : 0u;
+        uint32_t z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+          if (lane >= (uint32_t)o) z += y;
+        }
+        if (lane < (uint32_t)kTileWarps) wsum[lane] = z - w;
+      }
+      __syncthreads();
+      const uint32_t e = wsum[warp] + s - c0 - c1;
+      if (x0 < nb) {
+        toff[x0] = e;
+        tcnt[x0] = c0;
+        base[x0] = cur0;
+        cur0 += c0;
+      }
+      if (x0 + 1 < nb) {
+        toff[x0 + 1] = e + c0;
+        tcnt[x0 + 1] = c1;
+        base[x0 + 1] = cur1;
+        cur1 += c1;
+      }
+    }
+    fetch(t0 + T);  // next tile, in flight meanwhile
+    __syncthreads();
+    Wd* d0 = dw + t0 * W;
+    if constexpr (STAGE) {
+      for (uint32_t b = warp; b < nb; b += kTileWarps) {
+        const uint32_t c = tcnt[b] * W;
+        const Wd* g = iw + (uint64_t)base[b] * W;
+        Wd* s = stage + toff[b] * W;
+        if constexpr (WB >= 4) {
+          for (uint32_t u = lane; u < c; u += 32) cp_async<WB>(s + u, g + u);
+        } else {
+          for (uint32_t u = lane; u < c; u += 32) s[u] = g[u];
+        }
+      }
+      if constexpr (WB >= 4) cp_async_wait_all();
+      __syncthreads();
+      const uint32_t total = tn * W;
+      if constexpr (VEC) {
+        // 16-byte chunk c = words [V*c, V*c + V) of the tile's destination
+        constexpr uint32_t V = 16 / WB;
+        const uint32_t C = total / V;
+        uint4* dv = reinterpret_cast<uint4*>(d0);
+        for (uint32_t c = threadIdx.x; c < C; c += kTileThreads) {
+          const uint32_t t = c * V;
+          uint32_t j = (uint32_t)fdiv(t, fdW), w = t - j * W;
+          Wd x[V];
+#pragma unroll
+          for (uint32_t k = 0; k < V; ++k) {
+            x[k] = stage[(uint32_t)pos[j] * W + w];
+            if (++w == W) {
+              w = 0;
+              ++j;
+            }
+          }
+          if constexpr (WB == 4) dv[c] = make_uint4(x[0], x[1], x[2], x[3]);
+          else dv[c] = make_uint4(x[0].x, x[0].y, x[1].x, x[1].y);
+        }
+        for (uint32_t t = C * V + threadIdx.x; t < total; t += kTileThreads) {
+          const uint32_t j = (uint32_t)fdiv(t, fdW), w = t - j * W;
+          d0[t] = stage[(uint32_t)pos[j] * W + w];
+        }
+      } else {
+        for (uint32_t t = threadIdx.x; t < total; t += kTileThreads) {
+          const uint32_t j = (uint32_t)fdiv(t, fdW), w = t - j * W;
+          d0[t] = stage[(uint32_t)pos[j] * W + w];
+        }
+      }
+    } else {
+      // pos[] holds the inverse: sorted entry q belongs to tile rid pos[q]
+      for (uint32_t b = warp; b < nb; b += kTileWarps) {
+        const uint32_t c = tcnt[b] * W;
+        const Wd* g = iw + (uint64_t)base[b] * W;
+        const uint32_t q0 = toff[b];
+        for (uint32_t u = lane; u < c; u += 32) {
+          const uint32_t q = (uint32_t)fdiv(u, fdW), w = u - q * W;
+          d0[(uint64_t)pos[q0 + q] * W + w] = g[u];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  }
+}
+
+
+// ------------------------------------------------------------------ host side
+
+// Variant 4 (L2 runs): k_hist_runs -> k_run_scan -> k_part_runs -> k_probe_l2
+// (Phase II gather in run order) -> k_unpart_runs.
+struct Layout4 {
+  uint32_t sl, nb, G, T;
+  uint64_t per, tiles;
+  bool stage_mode, strided;
+  size_t b_cnt, b_tot, b_off, b_ctr, b_run, b_tpos, b_tcnt, b_rc, b_stage, need;
+};
+
+// Tile of the L2-run plan (Phase I and III): the largest power of two up to
+// 4096 rids whose records fit kUnpartStageMax bytes of shared memory (at least
+// 512 rids); larger records are not staged, 2048 rids per tile.
+inline void part_tile(uint32_t rec, uint32_t& T, bool& stage) {
+  T = kTileThreads * kPartIpt;
+  while (T > (uint32_t)kTileThreads && (uint64_t)T * rec > kUnpartStageMax) T >>= 1;
+  stage = (uint64_t)T * rec <= kUnpartStageMax;
+  if (!stage) T = 2048;
+}
+
+Layout4 layout4(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool strided) {
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  Layout4 L;
+  L.sl = (uint32_t)plan.seg_log2;
+  L.nb = (uint32_t)((r.n_src + (1ull << L.sl) - 1) >> L.sl);
+  part_tile(r.rec, L.T, L.stage_mode);
+  // CTA ranges: whole 4096-rid blocks (every tile starts at a multiple of T),
+  // kL2Ranges per SM so that every resident count of 2, 3 or 4 CTAs per SM
+  // takes the same number of ranges
+  const uint64_t block = (uint64_t)kTileThreads * kPartIpt;
+  const uint64_t g_max = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)ctx.sms * kL2Ranges,
+                                                                  (r.n + block - 1) / block));
+  L.per = ((r.n + g_max - 1) / g_max + block - 1) / block * block;
+  L.G = (uint32_t)((r.n + L.per - 1) / L.per);
+  L.tiles = (r.n + L.T - 1) / L.T;
+  L.strided = strided;
+  L.b_cnt = al((size_t)L.nb * L.G * 4);
+  L.b_tot = al((size_t)L.nb * 4);
+  L.b_off = al(((size_t)L.nb + 1) * 4);
+  L.b_ctr = 256;
+  L.b_run = al(r.n * 4);
+  L.b_tpos = al(r.n * 2);
+  L.b_tcnt = al((size_t)L.tiles * L.nb * 2);
+  L.b_rc = strided ? al(r.n * 4) : 0;
+  L.b_stage = al(r.n * r.rec);
+  L.need = L.b_cnt + L.b_tot + L.b_off + L.b_ctr + L.b_run + L.b_tpos + L.b_tcnt + L.b_rc + L.b_stage;
+  return L;
+}
+
+template <int WB, bool VEC>
+void launch_unpart(dpg_ctx& ctx, const Layout4& L, uint64_t n, uint32_t rec, const uint32_t* off,
+                   const uint32_t* cnt, const uint16_t* tpos, const uint16_t* tcnt, const uint8_t* internal,
+                   uint8_t* dst, cudaStream_t st) {
+  const uint32_t W = rec / WB;
+  const FastDiv f = make_fastdiv(W);
+  const size_t smem = (((size_t)L.nb * 12 + 15) & ~size_t(15)) + 2 * (size_t)L.T +
+                      (L.stage_mode ? (size_t)L.T * rec : 0);
+#define DPG_UNPART(IPTV, STG)                                                                                  \
+  {                                                                                                            \
+    auto kern = k_unpart_runs<WB, IPTV, STG, VEC && STG>;                                                      \
+    set_smem(kern, smem);                                                                                      \
+    const uint32_t grid = std::min<uint32_t>(L.G, ctx.sms * resident_per_sm(kern, kTileThreads, smem));        \
+    kern<<<grid, kTileThreads, smem, st>>>(n, L.nb, L.G, L.per, off, cnt, tpos, tcnt, internal, dst, W, f,     \
+                                           ctx.d_err);                                                         \
+  }
+  if (!L.stage_mode) DPG_UNPART(4, false)
+  else if (L.T == 4096) DPG_UNPART(8, true)
+  else if (L.T == 2048) DPG_UNPART(4, true)
+  else if (L.T == 1024) DPG_UNPART(2, true)
+  else DPG_UNPART(1, true)
+#undef DPG_UNPART
+}
+
+template <class Rid>
+int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
+  const bool strided = !std::is_same<Rid, RidArray>::value;
+  const Layout4 L = layout4(ctx, r, plan, strided);
+  const uint32_t sl = L.sl, nb = L.nb, G = L.G;
+  if (nb > kL2MaxRuns) return DPG_EINVAL;
+  if (int s = ensure_scratch(ctx, L.need)) return s;
+  uint8_t* p = static_cast<uint8_t*>(ctx.scratch);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(p); p += L.b_cnt;
+  uint32_t* tot = reinterpret_cast<uint32_t*>(p); p += L.b_tot;
+  uint32_t* off = reinterpret_cast<uint32_t*>(p); p += L.b_off;
+  unsigned long long* pctr = reinterpret_cast<unsigned long long*>(p); p += L.b_ctr;
+  uint32_t* run_rid = reinterpret_cast<uint32_t*>(p); p += L.b_run;
+  uint16_t* tpos = reinterpret_cast<uint16_t*>(p); p += L.b_tpos;
+  uint16_t* tcnt = reinterpret_cast<uint16_t*>(p); p += L.b_tcnt;
+  int32_t* rc = strided ? reinterpret_cast<int32_t*>(p) : nullptr; p += L.b_rc;
+  uint8_t* stage = p;
+  cudaError_t e = cudaMemsetAsync(tot, 0, (size_t)nb * 4, r.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pctr, 0, 8, r.stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  {
+    TraceScope ts(ctx, "k_hist_runs", r.stream);
+    const size_t smem = (size_t)nb * 4;
+    if (!strided && reinterpret_cast<uintptr_t>(r.rids.base) % 16 == 0) {
+      set_smem(k_hist_runs4, smem);
+      const uint32_t grid = std::min<uint32_t>(G, ctx.sms * resident_per_sm(k_hist_runs4, kTileThreads, smem));
+      k_hist_runs4<<<grid, kTileThreads, smem, r.stream>>>(reinterpret_cast<const int32_t*>(r.rids.base), r.n,
+                                                           (uint32_t)r.n_src, sl, nb, G, L.per, cnt, tot, ctx.d_err);
+    } else {
+      auto kern = k_hist_runs<Rid>;
+      set_smem(kern, smem);
+      const uint32_t grid = std::min<uint32_t>(G, ctx.sms * resident_per_sm(kern, kTileThreads, smem));
+      kern<<<grid, kTileThreads, smem, r.stream>>>(rid, r.n, (uint32_t)r.n_src, sl, nb, G, L.per, cnt, tot,
+                                                   ctx.d_err, rc);
+    }
+  }
+  {
+    TraceScope ts(ctx, "k_run_scan", r.stream);
+    k_run_scan<<<1, 1024, 0, r.stream>>>(tot, nb, off, ctx.d_err);
+  }
+  const int32_t* ra = strided ? rc : reinterpret_cast<const int32_t*>(r.rids.base);
+  {
+    TraceScope ts(ctx, "k_part_runs", r.stream);
+    const size_t smem = (size_t)nb * 16 + (size_t)L.T * 4;  // cur, tcnt, toff, delta, ent
+#define DPG_PART(IPTV)                                                                                          \
+  {                                                                                                             \
+    auto kern = k_part_runs<IPTV>;                                                                              \
+    set_smem(kern, smem);                                                                                       \
+    const uint32_t grid = std::min<uint32_t>(G, ctx.sms * resident_per_sm(kern, kTileThreads, smem));           \
+    kern<<<grid, kTileThreads, smem, r.stream>>>(ra, r.n, sl, nb, G, L.per, off, cnt, run_rid, tpos, tcnt,      \
+                                                 ctx.d_err);                                                    \
+  }
+    if (L.T == 4096) DPG_PART(8)
+    else if (L.T == 2048) DPG_PART(4)
+    else if (L.T == 1024) DPG_PART(2)
+    else DPG_PART(1)
+#undef DPG_PART
+  }
+  ctx.launches += 4;
+  // Phase II: INTERNAL[k] = R[run_rid[k]], k in run order
+  const uint32_t wb2 = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.src)));
+  if (r.rec >= 64) {
+    launch_slot_gather(ctx, wb2, r.src, stage, run_rid, r.n, r.rec, (uint32_t)r.n_src, r.stream, "k_probe_l2");
+  } else {
+    TraceScope ts(ctx, "k_probe_l2", r.stream);
+    const uint32_t W = r.rec / wb2;
+    const FastDiv f = make_fastdiv(W);
+#define DPG_PR(WBV)                                                                                              \
+  {                                                                                                              \
+    auto kern = k_probe_runs<WBV>;                                                                               \
+    const uint32_t grid = ctx.sms * resident_per_sm(kern, kRunsGatherThreads, 0);                                    \
+    kern<<<grid, kRunsGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, pctr, ctx.d_err);              \
+  }
+    switch (wb2) {
+      case 16: DPG_PR(16) break;
+      case 8: DPG_PR(8) break;
+      case 4: DPG_PR(4) break;
+      case 2: DPG_PR(2) break;
+      default: DPG_PR(1) break;
+    }
+#undef DPG_PR
+    ctx.launches++;
+  }
+  // Phase III
+  {
+    TraceScope ts(ctx, "k_unpart_runs", r.stream);
+    const uint32_t wb3 = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
+    // 16-byte destination vectors: every tile starts at a multiple of 512
+    // rids, so at a 16-byte boundary of a 16-byte-aligned destination
+    const bool vec = pow2_align(reinterpret_cast<uintptr_t>(r.dst)) == 16 && r.rec >= 16;
+#define DPG_UNP(WBV, V) launch_unpart<WBV, V>(ctx, L, r.n, r.rec, off, cnt, tpos, tcnt, stage, r.dst, r.stream)
+    switch (wb3) {
+      case 16: DPG_UNP(16, false); break;
+      case 8:
+        if (vec) DPG_UNP(8, true);
+        else DPG_UNP(8, false);
+        break;
+      case 4:
+        if (vec) DPG_UNP(4, true);
+        else DPG_UNP(4, false);
+        break;
+      case 2: DPG_UNP(2, false); break;
+      default: DPG_UNP(1, false); break;
+    }
+#undef DPG_UNP
+    ctx.launches++;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "dpg l2 launch");
+  return DPG_OK;
+}
+
+}  // namespace
+
+int run_dpg_l2(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {
+  if (r.rids.stride == 4)
+    return run_dpg_l2_t<RidArray>(ctx, r, RidArray{reinterpret_cast<const int32_t*>(r.rids.base)}, plan);
+  return run_dpg_l2_t<RidStrided>(ctx, r, RidStrided{r.rids.base, r.rids.stride}, plan);
+}
+
+size_t l2_scratch_need(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool strided) {
+  return layout4(ctx, r, plan, strided).need;
+}
+
+}  // namespace dpg

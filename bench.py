@@ -54,6 +54,7 @@ def args_():
                    help="skip the 16-byte-record point (62,500,000 records, permutation rids) of the line")
     p.add_argument("--sweep-recs", default="16,32,64,100,256", help="record sizes of --sweep")
     p.add_argument("--sweep-impls", default="dpg_smem,dpg_l2,dpg_tuned,direct", help="implementations of --sweep")
+    p.add_argument("--sweep-bytes", type=float, default=1e9, help="source bytes per record size of --sweep")
     p.add_argument("--join", action="store_true",
                    help="foreign-key join workload (10,000,000 x 64-byte dimension, 200,000,000 x 16-byte fact, "
                         "Zipf 0.8): DPG-move, DPG-sort and direct; one JSON line; not the headline run")
@@ -246,7 +247,7 @@ def run_sweep(a):
     ctx = dpg.Context(0)
     stream = torch.cuda.current_stream(dev)
     for rec in [int(x) for x in a.sweep_recs.split(",")]:
-        n = 10 ** 9 // rec
+        n = int(a.sweep_bytes) // rec
         d_src = torch.from_numpy(synth.records(n, rec, 3)).to(dev)
         rids = synth.permutation(n, 2)
         d_rids = torch.from_numpy(rids).to(dev)

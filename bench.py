@@ -83,29 +83,34 @@ def args_():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one
-# ncu capture of the headline workload (n = 10,000,000, rec = 100, plan
-# variant 3), keyed by kernel; valid only while the kernel source hashes to
-# `src_sha256` (any edit of the retrieval kernels nulls the figure).
+# ncu capture of the headline workload (n = 10,000,000, rec = 100), keyed by
+# plan variant and kernel (L2-run plan captured with 65,536-record runs, the
+# 3-pass plan with 512-record segments; the run length does not change what
+# these kernels read and write); valid only while the retrieval sources hash
+# to `src_sha256` (any edit of them nulls the figure).
 NCU_TRAFFIC = {
-    "src_sha256": "9233aa1a4181b33b2bee26c08d4c52fdd2acb11f005637f4c4e01cdacb8d385b"
+    "src_sha256": "7b8b5948b0c760b5dfdfb7f0758a2febfb6365c3841b50c1ad3ffe707761a93f"
+                  ":fed33f4b0ef0c37f8a8a490451b686f648d512054101b74b235a4e323857d718"
                   ":5eccae304881b1c2197a96b3d20def24e4f4fdac52f01beaf026764ec77fd6c2",
     "n": 10_000_000, "rec": 100,
-    "bytes": {"k_probe": 1020184832 + 946568448, "k_gather_phase3": 1040505344 + 955376384},
+    "bytes": {"4/k_probe_l2": 1040055808 + 959607296, "4/k_gather_phase3": 1059375104 + 954893824,
+              "3/k_probe": 1020238336 + 944367872, "3/k_gather_phase3": 1040485120 + 955574272},
 }
+TRAFFIC_SOURCES = ("dpg_retrieve.cu", "dpg_runs.cu", "dpg_device.cuh")
 
 
 def kernel_src_sha256() -> str:
     import hashlib
     d = os.path.join(ROOT, "paper_cs_0308004_gb300", "csrc")
-    return ":".join(hashlib.sha256(open(os.path.join(d, f), "rb").read()).hexdigest()
-                    for f in ("dpg_retrieve.cu", "dpg_device.cuh"))
+    return ":".join(hashlib.sha256(open(os.path.join(d, f), "rb").read()).hexdigest() for f in TRAFFIC_SOURCES)
 
 
-def ncu_traffic(kernel: str, n: int, rec: int, variant: int):
+def ncu_traffic(kernel: str, n: int, rec: int, plan):
     t = NCU_TRAFFIC
-    if (n, rec, variant) != (t["n"], t["rec"], 3) or kernel not in t["bytes"]:
+    key = f"{plan[0]}/{kernel}"
+    if (n, rec) != (t["n"], t["rec"]) or key not in t["bytes"]:
         return None
-    return t["bytes"][kernel] if kernel_src_sha256() == t["src_sha256"] else None
+    return t["bytes"][key] if kernel_src_sha256() == t["src_sha256"] else None
 
 
 def hbm_peak():
@@ -208,14 +213,22 @@ def job_gbs(world: int, bytes_per_rank: int, max_ms: float) -> float:
 
 
 def per_kernel_bytes(n, n_src, rec, stride):
-    """Algorithmic bytes each kernel must move (per launch)."""
+    """Algorithmic bytes each kernel must move (per launch).  3-pass and 2-pass
+    plans: k_hist .. k_probe_scatter; L2-run plan: k_hist_runs .. k_unpart_runs
+    (slot mode for records of 96 bytes and more, tile places below)."""
+    compact = 4 * n if stride != 4 else 0       # strided rids are copied out once
+    slot = rec >= 96
     return {
-        "k_hist": n * stride,
-        "k_distribute": n * stride + 2 * n + 4 * n,
+        "k_hist": n * stride + compact,
+        "k_distribute": 4 * n + 2 * n + 4 * n,
         "k_probe": 2 * n + n_src * rec + n * rec,
         "k_probe_scatter": 6 * n + n_src * rec + n * rec,
         "k_gather_phase3": 4 * n + 2 * n * rec,
         "k_gather_direct": n * stride + 2 * n * rec,
+        "k_hist_runs": n * stride + compact,
+        "k_part_runs": 4 * n + 4 * n + (4 * n if slot else 2 * n),
+        "k_probe_l2": 4 * n + n_src * rec + n * rec,
+        "k_unpart_runs": 2 * n + 2 * n * rec,
     }
 
 
@@ -786,7 +799,7 @@ def main():
                           "what": "dpg_sort_records: extract pairs + stable 10-pass LSD radix sort + DPG copy"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": ncu_traffic(dom, n, rec, plan[0]),
+                         "traffic": ncu_traffic(dom, n, rec, plan),
                          "algorithmic_bytes": kb.get(dom, 0)},
             "kernels": kernels,
             "cpu_baseline": cpu,

@@ -77,11 +77,11 @@ const char* dpg_last_error(dpg_ctx* ctx);
  * II copies each run's records out in run order while the run sits in fast
  * memory, Phase III writes the destination in rid order.  n == 0 is a no-op.
  * Duplicated and skewed rids are allowed (§2, §2.3).  The plan is the one
- * dpg_tune cached for this shape, else chosen by record size: below 96 bytes
- * runs of about 16 MB held in the L2 (tile counting sort in Phase I, tile-wise
- * rebuild in Phase III); from 96 bytes runs of up to 104 KB held in one CTA's
- * shared memory, with an INTERNAL staging table (3-pass) below 192 bytes and
- * records written straight to their destination (2-pass) from 192 bytes.
+ * dpg_tune cached for this shape, else chosen by record size: below 192 bytes
+ * runs of about 16 MB held in the L2 (tile counting sort in Phase I; Phase III
+ * rebuilds the destination tile by tile below 96 bytes, through a 4-byte slot
+ * per rid from 96 bytes); from 192 bytes runs of up to 104 KB held in one
+ * CTA's shared memory, records written straight to their destination (2-pass).
  */
 dpg_status dpg_retrieve(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes,
                         size_t n, const int32_t* rids, void* dst, void* stream);

@@ -811,9 +811,9 @@ Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
     }
   }
   // Untuned default by record size, from the 1e9-byte permutation sweep
-  // (16..64 B: L2 runs; 100 B: shared-memory segments, 3-pass; 256 B: 2-pass).
-  // Forcing a segment size or chunk keeps the shared-memory plan.
-  int dflt = r.rec < 96 ? 4 : (r.rec < 192 ? 3 : 2);
+  // (16..128 B: L2 runs; 256 B: 2-pass shared-memory segments).  Forcing a
+  // segment size or chunk keeps the shared-memory plan.
+  int dflt = r.rec < 192 ? 4 : 2;
   if (std::getenv("DPG_SEG_LOG2") || std::getenv("DPG_CHUNK")) dflt = 3;
   p.variant = env_int("DPG_VARIANT", dflt);
   const int o = env_int("DPG_SEG_LOG2", -1);

@@ -202,14 +202,16 @@ __global__ void __launch_bounds__(1024)
 // Phase I, pass 2 of the L2-run plan.  CTA g appends the rids of
 // [g*per, (g+1)*per) to their runs at its cursors cur_g[g*nb + b], T rids at a
 // time: the tile is counting-sorted by run in shared memory and written to the
-// runs as contiguous pieces.  For Phase III it records each rid's place in its
-// sorted tile, tpos[i] (u16), and the tile's count of each run,
-// tcnt_g[tile*nb + b] (u16), tile = i / T.
-template <int IPT>
+// runs as contiguous pieces.  For Phase III it records either each rid's place
+// in its sorted tile, tpos[i] (u16), and the tile's count of each run,
+// tcnt_g[tile*nb + b] (u16), tile = i / T; or, with SLOT, each rid's place in
+// INTERNAL, slot[i] (u32).
+template <int IPT, bool SLOT>
 __global__ void __launch_bounds__(kTileThreads, 3)
     k_part_runs(const int32_t* __restrict__ rid, uint64_t n, uint32_t sl, uint32_t nb, uint32_t G, uint64_t per,
                 const uint32_t* __restrict__ off, const uint32_t* __restrict__ cur_g, uint32_t* __restrict__ run_rid,
-                uint16_t* __restrict__ tpos, uint16_t* __restrict__ tcnt_g, const int* err) {
+                uint16_t* __restrict__ tpos, uint16_t* __restrict__ tcnt_g, uint32_t* __restrict__ slot,
+                const int* err) {
   constexpr uint32_t T = kTileThreads * IPT;
   extern __shared__ __align__(16) uint8_t sm[];
   __shared__ uint32_t wsum[32];
@@ -259,19 +261,23 @@ __global__ void __launch_bounds__(kTileThreads, 3)
       uint16_t* tc = tcnt_g + (t0 / T) * nb;
       for (uint32_t x = tid; x < nb; x += kTileThreads) {
         const uint32_t c = tcnt[x];
-        tc[x] = (uint16_t)c;
+        if (!SLOT) tc[x] = (uint16_t)c;
         delta[x] = cur[x] - toff[x];
         cur[x] += c;
         tcnt[x] = 0;
       }
+      if (SLOT) __syncthreads();  // delta[] is read below
       uint16_t* tp = tpos + t0;
+      uint32_t* sp = slot + t0;
 #pragma unroll
       for (int k = 0; k < IPT; ++k) {
         const uint32_t j = k * kTileThreads + tid;
         if (full || j < tn) {
-          const uint32_t p = toff[r[k] >> sl] + l[k];
+          const uint32_t b = r[k] >> sl;
+          const uint32_t p = toff[b] + l[k];
           ent[p] = r[k];
-          tp[j] = (uint16_t)p;
+          if (SLOT) sp[j] = delta[b] + p;
+          else tp[j] = (uint16_t)p;
         }
       }
       __syncthreads();
@@ -516,7 +522,7 @@ __global__ void __launch_bounds__(kTileThreads)
 struct Layout4 {
   uint32_t sl, nb, G, T;
   uint64_t per, tiles;
-  bool stage_mode, strided;
+  bool stage_mode, slot_mode, strided;
   size_t b_cnt, b_tot, b_off, b_ctr, b_run, b_tpos, b_tcnt, b_rc, b_stage, need;
 };
 
@@ -524,9 +530,10 @@ struct Layout4 {
 // 4096 rids whose records fit kUnpartStageMax bytes of shared memory (at least
 // 512 rids); larger records are not staged, 2048 rids per tile.
 inline void part_tile(uint32_t rec, uint32_t& T, bool& stage) {
+  const uint64_t smax = (uint64_t)env_int("DPG_UNPART_STAGE_MAX", (int)kUnpartStageMax);
   T = kTileThreads * kPartIpt;
-  while (T > (uint32_t)kTileThreads && (uint64_t)T * rec > kUnpartStageMax) T >>= 1;
-  stage = (uint64_t)T * rec <= kUnpartStageMax;
+  while (T > (uint32_t)kTileThreads && (uint64_t)T * rec > smax) T >>= 1;
+  stage = (uint64_t)T * rec <= smax;
   if (!stage) T = 2048;
 }
 
@@ -545,14 +552,18 @@ Layout4 layout4(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool s
   L.per = ((r.n + g_max - 1) / g_max + block - 1) / block * block;
   L.G = (uint32_t)((r.n + L.per - 1) / L.per);
   L.tiles = (r.n + L.T - 1) / L.T;
+  // Phase III: records of 96 bytes and more are gathered through a 4-byte
+  // INTERNAL slot per rid (the 3-pass gather); smaller ones are rebuilt tile
+  // by tile from 2-byte tile places
+  L.slot_mode = env_int("DPG_L2_SLOT", r.rec >= 96 ? 1 : 0) != 0;
   L.strided = strided;
   L.b_cnt = al((size_t)L.nb * L.G * 4);
   L.b_tot = al((size_t)L.nb * 4);
   L.b_off = al(((size_t)L.nb + 1) * 4);
   L.b_ctr = 256;
   L.b_run = al(r.n * 4);
-  L.b_tpos = al(r.n * 2);
-  L.b_tcnt = al((size_t)L.tiles * L.nb * 2);
+  L.b_tpos = al(r.n * (L.slot_mode ? 4 : 2));
+  L.b_tcnt = L.slot_mode ? 0 : al((size_t)L.tiles * L.nb * 2);
   L.b_rc = strided ? al(r.n * 4) : 0;
   L.b_stage = al(r.n * r.rec);
   L.need = L.b_cnt + L.b_tot + L.b_off + L.b_ctr + L.b_run + L.b_tpos + L.b_tcnt + L.b_rc + L.b_stage;
@@ -596,7 +607,9 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   uint32_t* off = reinterpret_cast<uint32_t*>(p); p += L.b_off;
   unsigned long long* pctr = reinterpret_cast<unsigned long long*>(p); p += L.b_ctr;
   uint32_t* run_rid = reinterpret_cast<uint32_t*>(p); p += L.b_run;
-  uint16_t* tpos = reinterpret_cast<uint16_t*>(p); p += L.b_tpos;
+  uint16_t* tpos = reinterpret_cast<uint16_t*>(p);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(p);  // the same piece in slot mode
+  p += L.b_tpos;
   uint16_t* tcnt = reinterpret_cast<uint16_t*>(p); p += L.b_tcnt;
   int32_t* rc = strided ? reinterpret_cast<int32_t*>(p) : nullptr; p += L.b_rc;
   uint8_t* stage = p;
@@ -629,11 +642,11 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
     const size_t smem = (size_t)nb * 16 + (size_t)L.T * 4;  // cur, tcnt, toff, delta, ent
 #define DPG_PART(IPTV)                                                                                          \
   {                                                                                                             \
-    auto kern = k_part_runs<IPTV>;                                                                              \
+    auto kern = L.slot_mode ? k_part_runs<IPTV, true> : k_part_runs<IPTV, false>;                               \
     set_smem(kern, smem);                                                                                       \
     const uint32_t grid = std::min<uint32_t>(G, ctx.sms * resident_per_sm(kern, kTileThreads, smem));           \
     kern<<<grid, kTileThreads, smem, r.stream>>>(ra, r.n, sl, nb, G, L.per, off, cnt, run_rid, tpos, tcnt,      \
-                                                 ctx.d_err);                                                    \
+                                                 slot, ctx.d_err);                                              \
   }
     if (L.T == 4096) DPG_PART(8)
     else if (L.T == 2048) DPG_PART(4)
@@ -667,7 +680,10 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
     ctx.launches++;
   }
   // Phase III
-  {
+  if (L.slot_mode) {
+    const uint32_t wb3 = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
+    launch_slot_gather(ctx, wb3, stage, r.dst, slot, r.n, r.rec, (uint32_t)r.n_src, r.stream, "k_gather_phase3");
+  } else {
     TraceScope ts(ctx, "k_unpart_runs", r.stream);
     const uint32_t wb3 = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
     // 16-byte destination vectors: every tile starts at a multiple of 512

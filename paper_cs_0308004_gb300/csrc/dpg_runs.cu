@@ -542,7 +542,11 @@ Layout4 layout4(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool s
   Layout4 L;
   L.sl = (uint32_t)plan.seg_log2;
   L.nb = (uint32_t)((r.n_src + (1ull << L.sl) - 1) >> L.sl);
-  part_tile(r.rec, L.T, L.stage_mode);
+  // Phase III: records of 96 bytes and more are gathered through a 4-byte
+  // INTERNAL slot per rid (the 3-pass gather), so Phase I takes its largest
+  // tile; smaller ones are rebuilt tile by tile from 2-byte tile places
+  L.slot_mode = env_int("DPG_L2_SLOT", r.rec >= 96 ? 1 : 0) != 0;
+  part_tile(L.slot_mode ? 1 : r.rec, L.T, L.stage_mode);
   // CTA ranges: whole 4096-rid blocks (every tile starts at a multiple of T),
   // kL2Ranges per SM so that every resident count of 2, 3 or 4 CTAs per SM
   // takes the same number of ranges
@@ -552,10 +556,6 @@ Layout4 layout4(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool s
   L.per = ((r.n + g_max - 1) / g_max + block - 1) / block * block;
   L.G = (uint32_t)((r.n + L.per - 1) / L.per);
   L.tiles = (r.n + L.T - 1) / L.T;
-  // Phase III: records of 96 bytes and more are gathered through a 4-byte
-  // INTERNAL slot per rid (the 3-pass gather); smaller ones are rebuilt tile
-  // by tile from 2-byte tile places
-  L.slot_mode = env_int("DPG_L2_SLOT", r.rec >= 96 ? 1 : 0) != 0;
   L.strided = strided;
   L.b_cnt = al((size_t)L.nb * L.G * 4);
   L.b_tot = al((size_t)L.nb * 4);

@@ -97,6 +97,55 @@ def test_l2_runs(ctx, monkeypatch, run_kb):
             check(ctx, src, rid_sequence(kind, n_src, 120_001 if kind != "perm" else n_src, 4), variants=("dpg",))
 
 
+@pytest.mark.parametrize("slot", ["0", "1"])
+@pytest.mark.parametrize("rec", [1, 8, 16, 24, 32, 64, 95, 96, 100, 128, 129, 255, 1000])
+def test_l2_runs_phase3_modes(ctx, monkeypatch, rec, slot):
+    """L2-run plan with either Phase III forced at every record size: the
+    4-byte slot gather, or the tile rebuild (shared-memory staging up to 128-byte
+    records, straight copies through the inverse tile places above)."""
+    monkeypatch.setenv("DPG_VARIANT", "4")
+    monkeypatch.setenv("DPG_L2_RUN_KB", "512")
+    monkeypatch.setenv("DPG_L2_SLOT", slot)
+    n_src = max(37, min(90_001, (4 << 20) // rec)) | 1
+    src = synth.records(n_src, rec, 17 + rec)
+    for kind, n in (("perm", n_src), ("dup", n_src + 4097), ("skew", 20_011)):
+        check(ctx, src, rid_sequence(kind, n_src, n, 3 + rec), variants=("dpg",))
+
+
+@pytest.mark.parametrize("stage_max", ["0", "16384"])
+def test_l2_runs_unstaged_and_small_stage(ctx, monkeypatch, stage_max):
+    """Tile rebuild without shared-memory staging (stage budget 0) and with
+    smaller tiles (16 KB budget), small records."""
+    monkeypatch.setenv("DPG_VARIANT", "4")
+    monkeypatch.setenv("DPG_L2_RUN_KB", "256")
+    monkeypatch.setenv("DPG_L2_SLOT", "0")
+    monkeypatch.setenv("DPG_UNPART_STAGE_MAX", stage_max)
+    for rec in (4, 16, 32, 48, 64):
+        n_src = 50_001
+        src = synth.records(n_src, rec, rec)
+        check(ctx, src, rid_sequence("dup", n_src, 70_003, rec), variants=("dpg",))
+
+
+@pytest.mark.parametrize("rid_off", [0, 1, 2, 3])
+@pytest.mark.parametrize("n", [4095, 4096, 4097, 12_289, 100_003])
+def test_l2_runs_rid_alignment_and_tiles(ctx, monkeypatch, rid_off, n):
+    """Rid arrays at every 4-byte offset from a 16-byte boundary (vector and
+    scalar histogram paths) and rid counts around the 4096-rid tile and range
+    sizes (partial last tiles)."""
+    monkeypatch.setenv("DPG_VARIANT", "4")
+    monkeypatch.setenv("DPG_L2_RUN_KB", "128")
+    n_src, rec = 33_333, 16
+    src = synth.records(n_src, rec, 5)
+    rids = synth.uniform_ids(n, n_src, n + rid_off)
+    want = oracle.retrieve(src, rids)
+    big = torch.zeros(n + 8, dtype=torch.int32, device=DEV)
+    d_rids = big[rid_off:rid_off + n]
+    d_rids.copy_(to_dev(rids))
+    out = ctx.retrieve(to_dev(src), d_rids)
+    ctx.sync()
+    assert np.array_equal(out.cpu().numpy(), want)
+
+
 @pytest.mark.parametrize("variant", ["3", "4"])
 @pytest.mark.parametrize("n_src,n", [(1, 1), (1, 1000), (2, 1), (5, 3), (1000, 1), (70000, 2)])
 def test_small_and_degenerate(ctx, monkeypatch, n_src, n, variant):

@@ -132,6 +132,11 @@ size_t l2_scratch_need(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan,
 void launch_slot_gather(dpg_ctx& ctx, uint32_t wb, const uint8_t* src, uint8_t* dst, const uint32_t* slot,
                         uint64_t n, uint32_t rec, uint32_t n_src, cudaStream_t st, const char* name);
 
+// Phase III of a join riding on a retrieval (r.join set): join rows from the
+// fact and dimension tables and INTERNAL (`stage`) read through `slot`
+// (dpg_retrieve.cu).
+void launch_join_phase3(dpg_ctx& ctx, const Retrieval& r, const uint8_t* stage, const uint32_t* slot);
+
 // Scratch arena helpers (dpg_api.cu).
 int ensure_scratch(dpg_ctx& ctx, size_t bytes);
 int ensure_aux(dpg_ctx& ctx, size_t bytes);

@@ -596,6 +596,22 @@ void launch_slot_gather(dpg_ctx& ctx, uint32_t wb, const uint8_t* src, uint8_t* 
   launch_gather<SlotArray, false>(ctx, wb, src, dst, SlotArray{slot}, n, rec, n_src, st, name);
 }
 
+void launch_join_phase3(dpg_ctx& ctx, const Retrieval& r, const uint8_t* stage, const uint32_t* slot) {
+  const JoinSpec& j = *r.join;
+  const uint32_t wb = std::min({pow2_align(j.fact_bytes), pow2_align(j.dim_bytes),
+                                pow2_align(reinterpret_cast<uintptr_t>(j.out)),
+                                pow2_align(reinterpret_cast<uintptr_t>(j.fact)),
+                                pow2_align(reinterpret_cast<uintptr_t>(j.dim))});
+  if (j.mode == 0)
+    launch_join_rows<RowIdentity, RowSlot, false>(ctx, "k_join_move_rows", wb, j.fact, RowIdentity{}, j.fact_bytes,
+                                                  stage, RowSlot{slot}, j.dim_bytes, j.n_dim, j.out, r.n, j.pk_off,
+                                                  0, r.stream);
+  else
+    launch_join_rows<RowSlot, RowPairKey, false>(ctx, "k_join_sort_rows", wb, stage, RowSlot{slot}, j.fact_bytes,
+                                                 j.dim, RowPairKey{j.sorted_pairs, j.key_bytes}, j.dim_bytes,
+                                                 j.n_dim, j.out, r.n, j.pk_off, 1, r.stream);
+}
+
 namespace {
 
 template <typename LoT, bool SCATTER, bool PK = false>
@@ -739,20 +755,7 @@ int run_dpg_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
     launch_probe<LoT, true>(ctx, wb_probe, r, sl, off, itemoff, nb, chunk, lo, side, r.dst, counter, use_bulk,
                             probe_smem);
   if (r.join) {
-    // Phase III writing join rows
-    const JoinSpec& j = *r.join;
-    const uint32_t wb = std::min({pow2_align(j.fact_bytes), pow2_align(j.dim_bytes),
-                                  pow2_align(reinterpret_cast<uintptr_t>(j.out)),
-                                  pow2_align(reinterpret_cast<uintptr_t>(j.fact)),
-                                  pow2_align(reinterpret_cast<uintptr_t>(j.dim))});
-    if (j.mode == 0)
-      launch_join_rows<RowIdentity, RowSlot, false>(ctx, "k_join_move_rows", wb, j.fact, RowIdentity{}, j.fact_bytes,
-                                                    stage, RowSlot{side}, j.dim_bytes, j.n_dim, j.out, r.n,
-                                                    j.pk_off, 0, r.stream);
-    else
-      launch_join_rows<RowSlot, RowPairKey, false>(ctx, "k_join_sort_rows", wb, stage, RowSlot{side}, j.fact_bytes,
-                                                   j.dim, RowPairKey{j.sorted_pairs, j.key_bytes}, j.dim_bytes,
-                                                   j.n_dim, j.out, r.n, j.pk_off, 1, r.stream);
+    launch_join_phase3(ctx, r, stage, side);
   } else if (three) {
     // Phase III
     const uint32_t wb = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
@@ -811,15 +814,22 @@ Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
     }
   }
   // Untuned default by record size, from the 1e9-byte permutation sweep
-  // (16..128 B: L2 runs; 256 B: 2-pass shared-memory segments).  Forcing a
-  // segment size or chunk keeps the shared-memory plan.
+  // (16..128 B: L2 runs; 256 B: 2-pass shared-memory segments).  Joins: the
+  // DPG-sort join moves fact rows like a retrieval (L2 runs: 24.0 against
+  // 27.6 ms on the 2e8-row Zipf workload); DPG-move probes each dimension
+  // row about 20 times under Zipf skew: the L2-run plan's cheaper Phase I
+  // (1.1 against 5.5 ms) goes to its Phase II, whose hot rows come from the L2
+  // rather than shared memory (7.4 against 2.4 ms), so the two tie (14.8 ms)
+  // and DPG-move keeps the 3-pass plan.
+  // Forcing a segment size or chunk keeps the shared-memory plan.
   int dflt = r.rec < 192 ? 4 : 2;
+  if (r.join) dflt = (r.join->mode == 1 && r.rec < 192) ? 4 : 3;
   if (std::getenv("DPG_SEG_LOG2") || std::getenv("DPG_CHUNK")) dflt = 3;
   p.variant = env_int("DPG_VARIANT", dflt);
   const int o = env_int("DPG_SEG_LOG2", -1);
   if (o >= 0 && (1ull << o) * r.rec <= kSegBytesMax) p.seg_log2 = o;
   p.chunk = (uint32_t)env_int("DPG_CHUNK", 0);
-  if (r.join) p.variant = 3;  // joins write join rows in the 3-pass Phase III
+  if (r.join && p.variant == 2) p.variant = 3;  // joins need INTERNAL and a slot per row
   if (p.variant == 4) p.seg_log2 = l2_seg_log2(r, (uint64_t)env_int("DPG_L2_RUN_KB", 16384) << 10);
   return p;
 }
@@ -854,7 +864,7 @@ size_t retrieve_scratch_need(const dpg_ctx& ctx, const Retrieval& r) {
   if (r.n == 0 || r.n_src == 0) return 0;
   const Plan plan = choose_plan(ctx, r);
   const bool strided = r.rids.stride != 4;
-  if (plan.variant == 4 && !r.join) return l2_scratch_need(ctx, r, plan, strided);
+  if (plan.variant == 4) return l2_scratch_need(ctx, r, plan, strided);
   return layout3(ctx, r, plan, plan.seg_log2 <= 16 ? 2 : 4, strided).need;
 }
 
@@ -868,7 +878,7 @@ int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "flag");
   }
-  if (plan.variant == 4 && !r.join) return run_dpg_l2(ctx, r, plan);
+  if (plan.variant == 4) return run_dpg_l2(ctx, r, plan);
   if ((1ull << plan.seg_log2) * r.rec > kSegBytesMax && plan.seg_log2 > 0) return DPG_EINVAL;
   const bool lo16 = plan.seg_log2 <= 16;
   if (r.rids.stride == 4) {

@@ -5,6 +5,7 @@
 // L = half the cache, here the GPU's shared L2).
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <type_traits>
 
 #include "dpg_device.cuh"
@@ -305,10 +306,27 @@ __global__ void __launch_bounds__(kTileThreads, 3)
 // (Larger records use the grid-stride gather over run order; having the L2
 // prefetch the next run with cp.async.bulk.prefetch was measured slower:
 // 590 against 442 us at 16 bytes.)
+// PK (DPG-move join, §4.2.1): each probed dimension row must carry its own
+// row number as the int64 little-endian key at byte pk_off; a row that does
+// not raises the range bit before any output row is written.
 template <int WB>
+__device__ __forceinline__ bool key_bytes_ok(const typename WordT<WB>::T& v, uint32_t w, uint32_t pk_off,
+                                             uint64_t key) {
+  uint8_t b[WB];
+  memcpy(b, &v, WB);
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < WB; ++j) {
+    const uint32_t pos = w * WB + j;
+    if (pos >= pk_off && pos < pk_off + 8) ok &= b[j] == (uint8_t)(key >> (8 * (pos - pk_off)));
+  }
+  return ok;
+}
+
+template <int WB, bool PK>
 __global__ void __launch_bounds__(kRunsGatherThreads, 4)
     k_probe_runs(const uint8_t* __restrict__ src, uint8_t* __restrict__ out, const uint32_t* __restrict__ run_rid,
-                 uint64_t n, uint32_t W, FastDiv fdW, unsigned long long* ctr, const int* err) {
+                 uint64_t n, uint32_t W, FastDiv fdW, unsigned long long* ctr, int* err, uint32_t pk_off) {
   using T = typename WordT<WB>::T;
   constexpr int U = WB == 16 ? 4 : kRunsGatherUnroll;  // words per thread per chunk (64 B of 16-byte words)
   constexpr uint32_t CH = kRunsGatherThreads * U;
@@ -333,6 +351,8 @@ __global__ void __launch_bounds__(kRunsGatherThreads, 4)
   load_ids(c, id);
   // The next chunk is claimed and its rids loaded while this chunk's source
   // reads are in flight.
+  bool bad = false;
+  const uint32_t pk_w0 = pk_off / WB, pk_w1 = (pk_off + 8 + WB - 1) / WB;
   for (int buf = 1; c < nch; buf ^= 1) {
     if (threadIdx.x == 0) s_c[buf] = atomicAdd(ctr, 1ull);
     const uint64_t base = c * CH + threadIdx.x;
@@ -343,6 +363,7 @@ __global__ void __launch_bounds__(kRunsGatherThreads, 4)
       if (t < total) {
         const uint32_t w = (uint32_t)(t - fdiv(t, fdW) * W);
         v[k] = s[(uint64_t)id[k] * W + w];
+        if (PK && w >= pk_w0 && w < pk_w1 && !key_bytes_ok<WB>(v[k], w, pk_off, id[k])) bad = true;
       }
     }
     __syncthreads();
@@ -355,6 +376,7 @@ __global__ void __launch_bounds__(kRunsGatherThreads, 4)
     }
     c = cn;
   }
+  if (PK && bad) atomicOr(err, ERR_RANGE);
 }
 
 // Phase III of the L2-run plan: CTA g rebuilds dst[i] for i in
@@ -545,7 +567,7 @@ Layout4 layout4(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool s
   // Phase III: records of 96 bytes and more are gathered through a 4-byte
   // INTERNAL slot per rid (the 3-pass gather), so Phase I takes its largest
   // tile; smaller ones are rebuilt tile by tile from 2-byte tile places
-  L.slot_mode = env_int("DPG_L2_SLOT", r.rec >= 96 ? 1 : 0) != 0;
+  L.slot_mode = r.join || env_int("DPG_L2_SLOT", r.rec >= 96 ? 1 : 0) != 0;  // join rows read through slots
   part_tile(L.slot_mode ? 1 : r.rec, L.T, L.stage_mode);
   // CTA ranges: whole 4096-rid blocks (every tile starts at a multiple of T),
   // kL2Ranges per SM so that every resident count of 2, 3 or 4 CTAs per SM
@@ -657,17 +679,19 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   ctx.launches += 4;
   // Phase II: INTERNAL[k] = R[run_rid[k]], k in run order
   const uint32_t wb2 = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.src)));
-  if (r.rec >= 64) {
+  const bool pk = r.join && r.join->mode == 0;
+  if (r.rec >= 64 && !pk) {
     launch_slot_gather(ctx, wb2, r.src, stage, run_rid, r.n, r.rec, (uint32_t)r.n_src, r.stream, "k_probe_l2");
   } else {
     TraceScope ts(ctx, "k_probe_l2", r.stream);
     const uint32_t W = r.rec / wb2;
     const FastDiv f = make_fastdiv(W);
+    const uint32_t pk_off = pk ? r.join->pk_off : 0u;
 #define DPG_PR(WBV)                                                                                              \
   {                                                                                                              \
-    auto kern = k_probe_runs<WBV>;                                                                               \
-    const uint32_t grid = ctx.sms * resident_per_sm(kern, kRunsGatherThreads, 0);                                    \
-    kern<<<grid, kRunsGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, pctr, ctx.d_err);              \
+    auto kern = pk ? k_probe_runs<WBV, true> : k_probe_runs<WBV, false>;                                         \
+    const uint32_t grid = ctx.sms * resident_per_sm(kern, kRunsGatherThreads, 0);                                \
+    kern<<<grid, kRunsGatherThreads, 0, r.stream>>>(r.src, stage, run_rid, r.n, W, f, pctr, ctx.d_err, pk_off);  \
   }
     switch (wb2) {
       case 16: DPG_PR(16) break;
@@ -680,7 +704,9 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
     ctx.launches++;
   }
   // Phase III
-  if (L.slot_mode) {
+  if (r.join) {
+    launch_join_phase3(ctx, r, stage, slot);
+  } else if (L.slot_mode) {
     const uint32_t wb3 = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));
     launch_slot_gather(ctx, wb3, stage, r.dst, slot, r.n, r.rec, (uint32_t)r.n_src, r.stream, "k_gather_phase3");
   } else {

@@ -57,12 +57,34 @@ def test_join_matches_oracle(ctx, n_dim, n_fact, s):
     run_all(ctx, dim, fact)
 
 
-@pytest.mark.parametrize("variant", ["2", "4"])
-def test_join_ignores_retrieval_plan(ctx, monkeypatch, variant):
-    """Joins always take the 3-pass DPG retrieval, whatever plan is set."""
+@pytest.mark.parametrize("run_kb", ["64", "4096"])
+@pytest.mark.parametrize("variant", ["2", "3", "4"])
+def test_join_retrieval_plans(ctx, monkeypatch, variant, run_kb):
+    """The same join rows whatever retrieval plan is set: the L2-run plan
+    (Phase III through INTERNAL slots, the DPG-move key check in Phase II),
+    the 3-pass plan, and the 2-pass plan, which falls back to the 3-pass plan
+    because join rows need INTERNAL."""
     monkeypatch.setenv("DPG_VARIANT", variant)
+    monkeypatch.setenv("DPG_L2_RUN_KB", run_kb)
     dim, fact, fk = synth.fk_tables(5000, 200_000, 64, 16, 0.8, 9)
     run_all(ctx, dim, fact)
+
+
+@pytest.mark.parametrize("variant", ["3", "4"])
+def test_join_bad_keys_each_plan(ctx, monkeypatch, variant):
+    """A referenced dimension row whose key is not its row number: DPG-move
+    reports it before writing any output row, on either plan."""
+    from paper_cs_0308004_gb300 import dpg
+    monkeypatch.setenv("DPG_VARIANT", variant)
+    dim, fact, fk = synth.fk_tables(3000, 80_000, 64, 16, 0.8, 12)
+    for pk_off, dim_bytes in ((0, 64), (3, 100), (56, 64)):
+        d, f = relayout(dim, fact, fk, 16, 0, dim_bytes, pk_off)
+        d[int(fk[123]), pk_off + 2] ^= 0x40                              # one byte of one referenced key
+        out = torch.full((80_000, 16 + dim_bytes), 0x33, dtype=torch.uint8, device=DEV)
+        ctx.fk_join(to_dev(f), to_dev(d), "move", 0, pk_off, out=out)
+        with pytest.raises(dpg.DpgRangeError):
+            ctx.sync()
+        assert bool((out == 0x33).all())
 
 
 @pytest.mark.parametrize("fact_bytes,fk_off,dim_bytes,pk_off", [(24, 8, 40, 16), (4, 0, 8, 0), (12, 4, 20, 12),

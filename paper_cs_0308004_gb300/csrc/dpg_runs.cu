@@ -18,6 +18,11 @@ namespace {
 constexpr int kRunsHistUnroll = 8;
 constexpr int kRunsGatherThreads = 256;
 constexpr int kRunsGatherUnroll = 8;
+// k_probe_runs: 16-byte words per thread per chunk (128 B in flight; 8 against
+// 4 measured 335 against 350 us at 32-byte records), and 3 CTAs per SM for
+// the registers that takes.
+constexpr int kProbeRunsU16 = 8;
+constexpr int kProbeRunsMinCtas = 3;
 
 // ------------------------------------------------------- L2-run plan (variant 4)
 // The paper sizes a run to half the cache (Figure 1, L = CACHE_SIZE/2).  On
@@ -324,11 +329,11 @@ __device__ __forceinline__ bool key_bytes_ok(const typename WordT<WB>::T& v, uin
 }
 
 template <int WB, bool PK>
-__global__ void __launch_bounds__(kRunsGatherThreads, 4)
+__global__ void __launch_bounds__(kRunsGatherThreads, kProbeRunsMinCtas)
     k_probe_runs(const uint8_t* __restrict__ src, uint8_t* __restrict__ out, const uint32_t* __restrict__ run_rid,
                  uint64_t n, uint32_t W, FastDiv fdW, unsigned long long* ctr, int* err, uint32_t pk_off) {
   using T = typename WordT<WB>::T;
-  constexpr int U = WB == 16 ? 4 : kRunsGatherUnroll;  // words per thread per chunk (64 B of 16-byte words)
+  constexpr int U = WB == 16 ? kProbeRunsU16 : kRunsGatherUnroll;  // words per thread per chunk
   constexpr uint32_t CH = kRunsGatherThreads * U;
   __shared__ uint64_t s_c[2];
   if (error_set(err)) return;

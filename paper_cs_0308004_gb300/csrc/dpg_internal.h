@@ -52,10 +52,14 @@ struct dpg_ctx {
 namespace dpg {
 
 // How a retrieval is carried out.
-//   variant 3: Phase I distribute -> Phase II probe into an INTERNAL staging
-//              table in run order -> Phase III gather in rid order (Figure 1).
-//   variant 2: Phase I distribute -> Phase II probe writing each record
-//              straight to its destination slot (probe and gather fused).
+//   variant 4: runs of a few MB held in the L2 (dpg_runs.cu): Phase I tile
+//              counting sort into at most kL2MaxRuns runs -> Phase II gather in
+//              run order -> Phase III tile rebuild or slot gather.
+//   variant 3: runs (segments) held in shared memory: Phase I distribute ->
+//              Phase II probe into an INTERNAL staging table in run order ->
+//              Phase III gather in rid order (Figure 1).
+//   variant 2: as variant 3, Phase II writing each record straight to its
+//              destination slot (probe and gather fused).
 struct Plan {
   int variant = 3;
   int seg_log2 = 10;     // a source segment (run) holds 2^seg_log2 records
@@ -109,7 +113,9 @@ constexpr uint32_t kSmemBuckets = 24576;      // Phase I per-CTA counters fit in
 constexpr uint32_t kL2MaxRuns = 1024;         // runs of the L2-run plan (variant 4)
 
 // Plan chosen for a retrieval: environment overrides (DPG_VARIANT,
-// DPG_SEG_LOG2, DPG_CHUNK, DPG_L2_RUN_KB) when set, else a plan dpg_tune
+// DPG_SEG_LOG2, DPG_CHUNK, DPG_L2_RUN_KB; DPG_L2_SLOT and
+// DPG_UNPART_STAGE_MAX pick the L2-run plan's Phase III, DPG_GATHER_CTAS the
+// grid of the grid-stride gathers) when set, else a plan dpg_tune
 // cached for the retrieval's shape, else the default for its record size.
 Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r);
 uint64_t plan_key(const Retrieval& r);

@@ -1,7 +1,8 @@
 """Parity of the CUDA retrieval path with the oracle, byte for byte.
 
-Every case compares dpg_retrieve (distribute-probe-gather, both the 3-pass and
-the 2-pass plan) and dpg_retrieve_direct with oracle.retrieve on the same
+Every case compares dpg_retrieve (distribute-probe-gather: the L2-run plan and
+the 3-pass and 2-pass shared-memory plans) and dpg_retrieve_direct with
+oracle.retrieve on the same
 seeded inputs: permutations, duplicates and skew (§2, §2.3), record sizes from
 1 to 4096 bytes, ragged tails, unaligned tables, forced small segments (the
 global-counter path and chunk splitting), empty and degenerate inputs, bad

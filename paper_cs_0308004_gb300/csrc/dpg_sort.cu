@@ -10,8 +10,9 @@
 // per pass (byte key_bytes-1 first, byte 0 last).  k_rs_global_hist counts
 // every key byte's digits over all pairs once (the counts do not depend on
 // the order).  Each pass is then one kernel, k_rs_onesweep: a CTA takes the
-// next tile of kRsTile pairs, ranks them stably (per-warp digit counts built
-// with __match_any_sync, prefix over warps), publishes its digit counts, and
+// next tile of kRsTile pairs, ranks them stably (per-warp digit counts, the
+// lanes sharing a digit found with a shared-memory OR, prefix over warps),
+// publishes its digit counts, and
 // finds how many pairs of each digit earlier tiles hold by looking back over
 // their published counts (decoupled look-back; every wait is bounded), then
 // reorders the tile in shared memory and writes each digit's pairs as one
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(kRsThreads, 3)
     k_rs_onesweep(const uint4* __restrict__ in, uint4* __restrict__ out, uint64_t n, uint32_t byte,
                   const uint32_t* __restrict__ digit_count, uint32_t* status, uint32_t* tile_ctr, int* err) {
   __shared__ uint16_t whist[kRsWarps][256];
+  __shared__ uint32_t wmask[kRsWarps][256];  // lanes of a warp holding digit d in this round
   __shared__ uint32_t tcnt[256], toff[256], s_base[256], s_excl[256];
   __shared__ uint32_t s_tile;
   extern __shared__ uint4 sbuf[];                              // kRsTile pairs
@@ -93,7 +95,10 @@ __global__ void __launch_bounds__(kRsThreads, 3)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
-  for (uint32_t x = threadIdx.x; x < kRsWarps * 256; x += kRsThreads) (&whist[0][0])[x] = 0;
+  for (uint32_t x = threadIdx.x; x < kRsWarps * 256; x += kRsThreads) {
+    (&whist[0][0])[x] = 0;
+    (&wmask[0][0])[x] = 0;
+  }
   __syncthreads();
   const uint32_t t = s_tile;
   const uint64_t base = (uint64_t)t * kRsTile;
@@ -126,12 +131,19 @@ __global__ void __launch_bounds__(kRsThreads, 3)
     const bool ok = e < n;
     if (ok) v[k] = in[e];
     d[k] = ok ? pair_digit(v[k], byte) : 256u + lane;  // unique sentinel per lane past the end
-    const uint32_t peers = __match_any_sync(0xffffffffu, d[k]);
+    // peers: the lanes of this warp with the same digit, gathered by a
+    // shared-memory OR (cheaper here than __match_any_sync)
+    if (ok) atomicOr(&wmask[warp][d[k]], 1u << lane);
+    __syncwarp();
+    const uint32_t peers = ok ? wmask[warp][d[k]] : (1u << lane);
     const uint32_t before = __popc(peers & lt);
     uint32_t prior = 0;
     if (ok) prior = whist[warp][d[k]];
     __syncwarp();
-    if (ok && before == 0) whist[warp][d[k]] = (uint16_t)(prior + __popc(peers));
+    if (ok && before == 0) {
+      whist[warp][d[k]] = (uint16_t)(prior + __popc(peers));
+      wmask[warp][d[k]] = 0;
+    }
     __syncwarp();
     rank[k] = prior + before;
   }

@@ -90,7 +90,7 @@ def args_():
 # to `src_sha256` (any edit of them nulls the figure).
 NCU_TRAFFIC = {
     "src_sha256": "571e77b214bee025b2b8a637f7b53acb85315437b4ef7399df27b1d9641f03ec"
-                  ":ea8c644061f50c9f8c3612cebb4a600fac8fd8af8fafd2ba396c2e904d0fac8f"
+                  ":40b0d4e4916b41b77f3966855ab96955f23f121315a75b199ba28530b129129e"
                   ":5eccae304881b1c2197a96b3d20def24e4f4fdac52f01beaf026764ec77fd6c2",
     "n": 10_000_000, "rec": 100,
     "bytes": {"4/k_probe_l2": 1040025344 + 959738880, "4/k_gather_phase3": 1061001216 + 955039744,

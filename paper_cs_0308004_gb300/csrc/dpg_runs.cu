@@ -1,7 +1,7 @@
 // DPG record retrieval with runs held in the L2 (plan variant 4): Phase I
 // partitions the rids into at most kL2MaxRuns runs of a few MB of source,
 // Phase II probes each run while its source bytes are L2-resident, Phase III
-// rebuilds the destination tile by tile (§2.1, Figure 1; run length: §2.1's
+// writes the destination in rid order (§2.1, Figure 1; run length: §2.1's
 // L = half the cache, here the GPU's shared L2).
 #include <algorithm>
 #include <cstdio>
@@ -28,19 +28,23 @@ constexpr int kProbeRunsMinCtas = 3;
 // The paper sizes a run to half the cache (Figure 1, L = CACHE_SIZE/2).  On
 // GB300 the cache that all SMs share is the 126 MB L2, so this plan uses at most
 // kL2MaxRuns runs of a few MB of source each.
-//   Phase I  (k_part_runs): each Phase I CTA walks its rid range in tiles of T
-//            rids; a tile is counting-sorted by run in shared memory and
-//            written to the runs as contiguous pieces at the CTA's cursors.
-//            Each rid's place in its sorted tile (tpos, 2 bytes) and the
-//            tile's count per run are kept for Phase III.
-//   Phase II (k_gather over run order): INTERNAL[k] = R[run_rid[k]]; the
-//            records in flight fall in one or two runs, whose source bytes
-//            stay L2-resident while they are probed.
-//   Phase III (k_unpart_runs): the mirror of Phase I.  A tile's entries of run
-//            b form one contiguous piece of INTERNAL (at the CTA's cursor for
-//            b), so the tile reads its pieces with coalesced loads into shared
-//            memory in sorted order and writes the destination in rid order
-//            through tpos.
+//   Phase I  (k_hist_runs, k_run_scan, k_part_runs): per CTA range the count
+//            of its rids per run; run offsets; then each range is walked in
+//            tiles of T rids, a tile counting-sorted by run in shared memory
+//            and written to the runs as contiguous pieces at the range's
+//            cursors.  For Phase III each rid keeps either its place in its
+//            sorted tile (2 bytes, plus the tile's count per run) or its place
+//            in INTERNAL (a 4-byte slot).
+//   Phase II (k_probe_runs below 64-byte records, the slot gather over run
+//            order from 64 bytes): INTERNAL[k] = R[run_rid[k]]; the records
+//            in flight fall in one or two runs, whose source bytes stay
+//            L2-resident while they are probed.
+//   Phase III (k_unpart_runs below 96-byte records): the mirror of Phase I.
+//            A tile's entries of run b form one contiguous piece of INTERNAL
+//            (at the range's cursor for b), so the tile reads its pieces with
+//            coalesced loads into shared memory in sorted order and writes
+//            the destination in rid order through the tile places.  From 96
+//            bytes, and for join rows, Phase III gathers through the slots.
 
 constexpr int kTileThreads = 512;
 constexpr int kTileWarps = kTileThreads / 32;

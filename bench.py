@@ -49,6 +49,8 @@ def args_():
     p.add_argument("--n", type=int, default=10_000_000)
     p.add_argument("--rec", type=int, default=100)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-lanes", type=int, default=3,
+                   help="contexts (each on its own host thread and stream) taking alternate end-to-end steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-small", action="store_true",
                    help="skip the 16-byte-record point (62,500,000 records, permutation rids) of the line")
@@ -734,7 +736,7 @@ def main():
         import threading
         h_src = torch.from_numpy(src).pin_memory()
         h_pairs = torch.from_numpy(pairs).pin_memory()
-        lanes = 2
+        lanes = max(1, a.e2e_lanes)
         ctxs = [ctx] + [dpg.Context(local) for _ in range(lanes - 1)]
         streams = [torch.cuda.Stream(dev) for _ in range(lanes)]
         outs = [torch.empty((n, rec), dtype=torch.uint8).pin_memory() for _ in range(lanes)]

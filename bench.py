@@ -665,6 +665,23 @@ def main():
     ms_dpg, launches, win = timed(lambda: ctx.sort_copy(d_pairs, d_src, out=d_out))
     ms_dir, launches_dir, win_dir = timed(lambda: ctx.sort_copy_direct(d_pairs, d_src, out=d_out))
 
+    # per-step distribution: 20 repetitions, each bracketed by its own CUDA
+    # events on the launching stream (after the timed region; not the headline)
+    def step_stats(fn, reps=20):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in evs:
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        ts = sorted(e0.elapsed_time(e1) for e0, e1 in evs)
+        return {"median_ms": round(statistics.median(ts), 4), "p90_ms": round(ts[int(0.9 * (reps - 1))], 4),
+                "min_ms": round(ts[0], 4), "reps": reps}
+
+    steps_dpg = step_stats(lambda: ctx.sort_copy(d_pairs, d_src, out=d_out))
+    steps_dir = step_stats(lambda: ctx.sort_copy_direct(d_pairs, d_src, out=d_out))
+
     # the whole §3 sort (extract + radix sort + DPG copy) and its phases 1-2 alone
     g_pairs = torch.empty_like(d_pairs)
     ms_keyptr, _, _ = timed(lambda: ctx.sort_keyptr(d_src, 10, out=g_pairs))
@@ -795,6 +812,7 @@ def main():
             "direct_gather": {"value": round(direct, 3), "unit": "GB/s", "ms_per_step": round(ms_dir, 4),
                               "pct_of_hbm_peak": round(direct / world / peak, 4)},
             "speedup_vs_direct": round(ms_dir / ms_dpg, 4),
+            "step_distribution": {"dpg": steps_dpg, "direct_gather": steps_dir},
             "small_records": small,
             "full_sort": {"ms_per_sort": round(ms_sortall, 4), "keyptr_sort_ms": round(ms_keyptr, 4),
                           "records_per_s": round(world * n / (ms_sortall * 1e-3), 1),

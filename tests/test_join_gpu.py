@@ -145,3 +145,16 @@ def test_join_large_sampled(ctx):
     order = keys * n_fact + rows
     assert bool((order[1:] > order[:-1]).all())
     assert torch.equal(srt, move[rows])
+
+
+@pytest.mark.parametrize("mode,variant", [("move", 3), ("sort", 4)])
+def test_join_default_plans(ctx, monkeypatch, mode, variant):
+    """Untuned joins: DPG-move on the 3-pass plan, DPG-sort on the L2-run plan."""
+    for name in ("DPG_VARIANT", "DPG_SEG_LOG2", "DPG_CHUNK", "DPG_L2_RUN_KB", "DPG_L2_SLOT"):
+        monkeypatch.delenv(name, raising=False)
+    dim, fact, fk = synth.fk_tables(4000, 90_001, 64, 16, 0.8, 13)
+    want = oracle.fk_join_sorted(fact, dim) if mode == "sort" else oracle.fk_join_move(fact, dim)
+    out = ctx.fk_join(to_dev(fact), to_dev(dim), mode)
+    ctx.sync()
+    assert ctx.last_plan()[0] == variant
+    assert np.array_equal(out.cpu().numpy(), want)

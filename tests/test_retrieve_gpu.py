@@ -355,3 +355,21 @@ def test_tune_then_retrieve(rec, stride):
         c.sync()
         assert c.last_plan() == (v, sl)
         assert np.array_equal(out.cpu().numpy(), oracle.retrieve(src, rids))
+
+
+@pytest.mark.parametrize("rec,variant", [(8, 4), (16, 4), (100, 4), (191, 4), (192, 2), (256, 2), (1000, 2)])
+def test_untuned_plan_by_record_size(monkeypatch, rec, variant):
+    """Without a tuned plan or overrides a retrieval takes the plan its record
+    size calls for (L2 runs below 192 bytes, 2-pass from 192), and still
+    matches the oracle."""
+    from paper_cs_0308004_gb300 import dpg
+    for name in ("DPG_VARIANT", "DPG_SEG_LOG2", "DPG_CHUNK", "DPG_L2_RUN_KB", "DPG_L2_SLOT"):
+        monkeypatch.delenv(name, raising=False)
+    with dpg.Context(0) as c:
+        n_src = 30_011
+        src = synth.records(n_src, rec, 8)
+        rids = synth.uniform_ids(40_009, n_src, 9)
+        out = c.retrieve(to_dev(src), to_dev(rids))
+        c.sync()
+        assert c.last_plan()[0] == variant
+        assert np.array_equal(out.cpu().numpy(), oracle.retrieve(src, rids))

@@ -28,11 +28,11 @@ constexpr int kProbeRunsMinCtas = 3;
 // The paper sizes a run to half the cache (Figure 1, L = CACHE_SIZE/2).  On
 // GB300 the cache that all SMs share is the 126 MB L2, so this plan uses at most
 // kL2MaxRuns runs of a few MB of source each.
-//   Phase I  (k_hist_runs, k_run_scan, k_part_runs): per CTA range the count
-//            of its rids per run; run offsets; then each range is walked in
-//            tiles of T rids, a tile counting-sorted by run in shared memory
-//            and written to the runs as contiguous pieces at the range's
-//            cursors.  For Phase III each rid keeps either its place in its
+//   Phase I  (k_hist_runs, k_part_runs): per CTA range the count of its
+//            rids per run; run offsets (scanned by every k_part_runs CTA);
+//            then each range is walked in tiles of T rids, a tile
+//            counting-sorted by run in shared memory and written to the runs
+//            as contiguous pieces at the range's cursors.  For Phase III each rid keeps either its place in its
 //            sorted tile (2 bytes, plus the tile's count per run) or its place
 //            in INTERNAL (a 4-byte slot).
 //   Phase II (k_probe_runs below 64-byte records, the slot gather over run
@@ -168,47 +168,6 @@ __global__ void __launch_bounds__(kTileThreads, 4)
   if (bad) atomicOr(err, ERR_RANGE);
 }
 
-// Exclusive scan over a block of 1024 threads; returns this thread's exclusive
-// prefix of v and sets *total (every thread) to the block sum.
-__device__ __forceinline__ uint32_t block1024_excl_scan(uint32_t v, uint32_t* wsum, uint32_t* total) {
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t s = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-    if (lane >= (uint32_t)o) s += y;
-  }
-  if (lane == 31) wsum[warp] = s;
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t w = wsum[lane];
-    uint32_t z = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
-      if (lane >= (uint32_t)o) z += y;
-    }
-    wsum[lane] = z - w;
-    if (lane == 31) wsum[32] = z;
-  }
-  __syncthreads();
-  const uint32_t e = wsum[warp] + s - v;
-  *total = wsum[32];
-  return e;
-}
-
-// off[b] = sum of tot[b'] for b' < b, off[nb] = n (nb <= 1024; one block).
-__global__ void __launch_bounds__(1024)
-    k_run_scan(const uint32_t* __restrict__ tot, uint32_t nb, uint32_t* __restrict__ off, const int* err) {
-  __shared__ uint32_t wsum[33];
-  if (error_set(err)) return;
-  const uint32_t v = threadIdx.x < nb ? tot[threadIdx.x] : 0u;
-  uint32_t total;
-  const uint32_t e = block1024_excl_scan(v, wsum, &total);
-  if (threadIdx.x < nb) off[threadIdx.x] = e;
-  if (threadIdx.x == 0) off[nb] = total;
-}
-
 // Phase I, pass 2 of the L2-run plan.  CTA g appends the rids of
 // [g*per, (g+1)*per) to their runs at its cursors cur_g[g*nb + b], T rids at a
 // time: the tile is counting-sorted by run in shared memory and written to the
@@ -219,9 +178,9 @@ __global__ void __launch_bounds__(1024)
 template <int IPT, bool SLOT>
 __global__ void __launch_bounds__(kTileThreads, 3)
     k_part_runs(const int32_t* __restrict__ rid, uint64_t n, uint32_t sl, uint32_t nb, uint32_t G, uint64_t per,
-                const uint32_t* __restrict__ off, const uint32_t* __restrict__ cur_g, uint32_t* __restrict__ run_rid,
-                uint16_t* __restrict__ tpos, uint16_t* __restrict__ tcnt_g, uint32_t* __restrict__ slot,
-                const int* err) {
+                const uint32_t* __restrict__ tot, uint32_t* __restrict__ off, const uint32_t* __restrict__ cur_g,
+                uint32_t* __restrict__ run_rid, uint16_t* __restrict__ tpos, uint16_t* __restrict__ tcnt_g,
+                uint32_t* __restrict__ slot, const int* err) {
   constexpr uint32_t T = kTileThreads * IPT;
   extern __shared__ __align__(16) uint8_t sm[];
   __shared__ uint32_t wsum[32];
@@ -230,11 +189,19 @@ __global__ void __launch_bounds__(kTileThreads, 3)
   uint32_t* tcnt = cur + nb;
   uint32_t* toff = tcnt + nb;
   uint32_t* delta = toff + nb;                      // cur[b] - toff[b] for the tile
-  uint32_t* ent = delta + nb;
+  uint32_t* runoff = delta + nb;                    // run b's first position in run_rid
+  uint32_t* ent = runoff + nb;
   const uint32_t tid = threadIdx.x;
+  // run offsets: exclusive scan of the run totals, in every CTA (block 0 also
+  // stores them for Phase III)
+  for (uint32_t x = tid; x < nb; x += kTileThreads) tcnt[x] = tot[x];
+  __syncthreads();
+  tile_scan(tcnt, runoff, nb, wsum);
+  if (blockIdx.x == 0)
+    for (uint32_t x = tid; x < nb; x += kTileThreads) off[x] = runoff[x];
   for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
     for (uint32_t x = tid; x < nb; x += kTileThreads) {
-      cur[x] = off[x] + cur_g[(uint64_t)g * nb + x];
+      cur[x] = runoff[x] + cur_g[(uint64_t)g * nb + x];
       tcnt[x] = 0;
     }
     __syncthreads();
@@ -548,7 +515,7 @@ __global__ void __launch_bounds__(kTileThreads)
 
 // ------------------------------------------------------------------ host side
 
-// Variant 4 (L2 runs): k_hist_runs -> k_run_scan -> k_part_runs -> k_probe_l2
+// Variant 4 (L2 runs): k_hist_runs -> k_part_runs -> k_probe_l2
 // (Phase II gather in run order) -> k_unpart_runs.
 struct Layout4 {
   uint32_t sl, nb, G, T;
@@ -663,20 +630,16 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
                                                    ctx.d_err, rc);
     }
   }
-  {
-    TraceScope ts(ctx, "k_run_scan", r.stream);
-    k_run_scan<<<1, 1024, 0, r.stream>>>(tot, nb, off, ctx.d_err);
-  }
   const int32_t* ra = strided ? rc : reinterpret_cast<const int32_t*>(r.rids.base);
   {
     TraceScope ts(ctx, "k_part_runs", r.stream);
-    const size_t smem = (size_t)nb * 16 + (size_t)L.T * 4;  // cur, tcnt, toff, delta, ent
+    const size_t smem = (size_t)nb * 20 + (size_t)L.T * 4;  // cur, tcnt, toff, delta, runoff, ent
 #define DPG_PART(IPTV)                                                                                          \
   {                                                                                                             \
     auto kern = L.slot_mode ? k_part_runs<IPTV, true> : k_part_runs<IPTV, false>;                               \
     set_smem(kern, smem);                                                                                       \
     const uint32_t grid = std::min<uint32_t>(G, ctx.sms * resident_per_sm(kern, kTileThreads, smem));           \
-    kern<<<grid, kTileThreads, smem, r.stream>>>(ra, r.n, sl, nb, G, L.per, off, cnt, run_rid, tpos, tcnt,      \
+    kern<<<grid, kTileThreads, smem, r.stream>>>(ra, r.n, sl, nb, G, L.per, tot, off, cnt, run_rid, tpos, tcnt, \
                                                  slot, ctx.d_err);                                              \
   }
     if (L.T == 4096) DPG_PART(8)
@@ -685,7 +648,7 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
     else DPG_PART(1)
 #undef DPG_PART
   }
-  ctx.launches += 4;
+  ctx.launches += 2;  // k_hist_runs, k_part_runs
   // Phase II: INTERNAL[k] = R[run_rid[k]], k in run order
   const uint32_t wb2 = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.src)));
   const bool pk = r.join && r.join->mode == 0;

@@ -92,11 +92,11 @@ def args_():
 # to `src_sha256` (any edit of them nulls the figure).
 NCU_TRAFFIC = {
     "src_sha256": "571e77b214bee025b2b8a637f7b53acb85315437b4ef7399df27b1d9641f03ec"
-                  ":40b0d4e4916b41b77f3966855ab96955f23f121315a75b199ba28530b129129e"
+                  ":ee1a37063262790b9aef4a6f8164a4320657f0073a54acf0791250ded4beb263"
                   ":5eccae304881b1c2197a96b3d20def24e4f4fdac52f01beaf026764ec77fd6c2",
     "n": 10_000_000, "rec": 100,
-    "bytes": {"4/k_probe_l2": 1040025344 + 959738880, "4/k_gather_phase3": 1061001216 + 955039744,
-              "3/k_probe": 1020236544 + 944038144, "3/k_gather_phase3": 1040706816 + 955483648},
+    "bytes": {"4/k_probe_l2": 1040025344 + 959676160, "4/k_gather_phase3": 1061674240 + 954808576,
+              "3/k_probe": 1020308736 + 945452544, "3/k_gather_phase3": 1040500224 + 955409408},
 }
 TRAFFIC_SOURCES = ("dpg_retrieve.cu", "dpg_runs.cu", "dpg_device.cuh")
 

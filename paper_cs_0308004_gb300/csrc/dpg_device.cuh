@@ -40,6 +40,51 @@ template <> struct WordT<4> { using T = uint32_t; };
 template <> struct WordT<2> { using T = uint16_t; };
 template <> struct WordT<1> { using T = uint8_t; };
 
+// The key check of the joins (§4.2.1): a dimension row must carry its own row
+// number as the int64 little-endian key at byte pk_off.  Word w of the row
+// (WB bytes at byte w*WB, overlapping that key: -8 < pk_off - w*WB < WB) is
+// checked by comparing its bytes, as two 64-bit halves, with the key shifted
+// to its place in the word, under the mask of the bytes the two share.
+template <int WB>
+__host__ __device__ __forceinline__ void word_halves(const typename WordT<WB>::T& v, uint64_t& lo, uint64_t& hi) {
+  if constexpr (WB == 16) {
+    lo = v.x | (uint64_t)v.y << 32;
+    hi = v.z | (uint64_t)v.w << 32;
+  } else if constexpr (WB == 8) {
+    lo = v.x | (uint64_t)v.y << 32;
+    hi = 0;
+  } else {
+    lo = v;
+    hi = 0;
+  }
+}
+
+template <int WB>
+__host__ __device__ __forceinline__ bool pk_word_ok(const typename WordT<WB>::T& v, uint32_t w, uint32_t pk_off,
+                                                    uint64_t key) {
+  uint64_t lo, hi;
+  word_halves<WB>(v, lo, hi);
+  const int s = (int)pk_off - (int)(w * WB);  // key byte b is byte s + b of the word
+  uint64_t klo, khi, mlo, mhi;
+  if (s <= 0) {
+    klo = key >> (-8 * s);
+    mlo = ~0ull >> (-8 * s);
+    khi = mhi = 0;
+  } else if (s < 8) {
+    klo = key << (8 * s);
+    mlo = ~0ull << (8 * s);
+    khi = key >> (64 - 8 * s);
+    mhi = ~0ull >> (64 - 8 * s);
+  } else {
+    klo = mlo = 0;
+    khi = key << (8 * (s - 8));
+    mhi = ~0ull << (8 * (s - 8));
+  }
+  if constexpr (WB < 8) mlo &= (1ull << (8 * WB)) - 1;
+  if constexpr (WB <= 8) mhi = 0;
+  return ((lo ^ klo) & mlo) == 0 && ((hi ^ khi) & mhi) == 0;
+}
+
 // Rid sources: a plain int32 array, or the int32 field of strided
 // key-pointer pairs.  Both address 4-byte-aligned int32 values.
 struct RidArray {

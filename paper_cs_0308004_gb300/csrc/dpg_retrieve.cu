@@ -456,20 +456,6 @@ struct RowPairKey {  // big-endian key bytes [0, kb) of sorted 16-byte pair r (k
   }
 };
 
-template <int WB>
-__device__ __forceinline__ bool pk_bytes_match(const typename WordT<WB>::T& v, uint32_t word, uint32_t pk_off,
-                                               uint64_t key) {
-  uint8_t b[WB];
-  memcpy(b, &v, WB);
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < WB; ++j) {
-    const uint32_t pos = word * WB + j;
-    if (pos >= pk_off && pos < pk_off + 8) ok &= b[j] == (uint8_t)(key >> (8 * (pos - pk_off)));
-  }
-  return ok;
-}
-
 template <int WB, class IA, class IB, bool CHECK_B>
 __global__ void __launch_bounds__(kGatherThreads)
     k_join_rows(const uint8_t* __restrict__ ta, IA ia, uint32_t wa, const uint8_t* __restrict__ tb, IB ib,
@@ -484,18 +470,20 @@ __global__ void __launch_bounds__(kGatherThreads)
   const uint64_t total = n * row_w;
   const uint64_t step = (uint64_t)gridDim.x * kGatherThreads * kGatherUnroll;
   const uint32_t pk_w0 = pk_off / WB, pk_w1 = (pk_off + 8 + WB - 1) / WB;
+  // word t = row r, word w of the row, walked in steps of kGatherThreads words
+  const uint32_t qs = (uint32_t)fdiv(kGatherThreads, fd_row), rs = kGatherThreads - qs * row_w;
   bool bad = false;
   for (uint64_t base = (uint64_t)blockIdx.x * kGatherThreads * kGatherUnroll + threadIdx.x; base < total;
        base += step) {
     T v[kGatherUnroll];
     bool ok[kGatherUnroll];
+    uint64_t r = fdiv(base, fd_row);
+    uint32_t w = (uint32_t)(base - r * row_w);
 #pragma unroll
     for (int k = 0; k < kGatherUnroll; ++k) {
       const uint64_t t = base + (uint64_t)k * kGatherThreads;
       ok[k] = false;
       if (t < total) {
-        const uint64_t r = fdiv(t, fd_row);
-        const uint32_t w = (uint32_t)(t - r * row_w);
         if (w < wa) {
           v[k] = a[ia(r) * wa + w];
           ok[k] = true;
@@ -505,11 +493,17 @@ __global__ void __launch_bounds__(kGatherThreads)
           if (!CHECK_B || key < nrows_b) {
             v[k] = bt[key * wb + wbw];
             ok[k] = true;
-            if (pk_check && wbw >= pk_w0 && wbw < pk_w1 && !pk_bytes_match<WB>(v[k], wbw, pk_off, key)) bad = true;
+            if (pk_check && wbw >= pk_w0 && wbw < pk_w1 && !pk_word_ok<WB>(v[k], wbw, pk_off, key)) bad = true;
           } else {
             bad = true;
           }
         }
+      }
+      r += qs;
+      w += rs;
+      if (w >= row_w) {
+        w -= row_w;
+        ++r;
       }
     }
 #pragma unroll

@@ -44,7 +44,10 @@ constexpr int kProbeRunsMinCtas = 3;
 //            (at the range's cursor for b), so the tile reads its pieces with
 //            coalesced loads into shared memory in sorted order and writes
 //            the destination in rid order through the tile places.  From 96
-//            bytes, and for join rows, Phase III gathers through the slots.
+//            bytes Phase III gathers through the slots; so do DPG-move join
+//            rows, while DPG-sort join rows are rebuilt tile by tile like
+//            records (fact rows up to 128 bytes), each followed by its
+//            dimension row.
 
 constexpr int kTileThreads = 512;
 constexpr int kTileWarps = kTileThreads / 32;
@@ -285,19 +288,6 @@ __global__ void __launch_bounds__(kTileThreads, 3)
 // PK (DPG-move join, §4.2.1): each probed dimension row must carry its own
 // row number as the int64 little-endian key at byte pk_off; a row that does
 // not raises the range bit before any output row is written.
-template <int WB>
-__device__ __forceinline__ bool key_bytes_ok(const typename WordT<WB>::T& v, uint32_t w, uint32_t pk_off,
-                                             uint64_t key) {
-  uint8_t b[WB];
-  memcpy(b, &v, WB);
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < WB; ++j) {
-    const uint32_t pos = w * WB + j;
-    if (pos >= pk_off && pos < pk_off + 8) ok &= b[j] == (uint8_t)(key >> (8 * (pos - pk_off)));
-  }
-  return ok;
-}
 
 template <int WB, bool PK>
 __global__ void __launch_bounds__(kRunsGatherThreads, kProbeRunsMinCtas)
@@ -339,7 +329,7 @@ __global__ void __launch_bounds__(kRunsGatherThreads, kProbeRunsMinCtas)
       if (t < total) {
         const uint32_t w = (uint32_t)(t - fdiv(t, fdW) * W);
         v[k] = s[(uint64_t)id[k] * W + w];
-        if (PK && w >= pk_w0 && w < pk_w1 && !key_bytes_ok<WB>(v[k], w, pk_off, id[k])) bad = true;
+        if (PK && w >= pk_w0 && w < pk_w1 && !pk_word_ok<WB>(v[k], w, pk_off, id[k])) bad = true;
       }
     }
     __syncthreads();
@@ -365,13 +355,34 @@ __global__ void __launch_bounds__(kRunsGatherThreads, kProbeRunsMinCtas)
 // 16-byte vectors when VEC (WB = 4 or 8, 16-byte-aligned destination).
 // Without STAGE (large records) each sorted entry is copied straight to its
 // destination record through the inverse of tpos.
-template <int WB, int IPT, bool STAGE, bool VEC>
+// JOIN (DPG-sort join rows, §4.2.1): the destination row of tile entry j is
+// the staged fact row || dimension row key(p), p = t0 + j, key(p) the
+// big-endian bytes [0, kb) of sorted pair p (staged beside the records); the
+// int64 little-endian key at byte pk_off of that dimension row must equal
+// key(p), else the range bit.  Rows are written as one word stream.
+struct JoinTail {
+  const uint8_t* dim;
+  const uint8_t* pairs;
+  uint32_t wd;  // dimension-row words
+  uint32_t kb;
+  uint32_t pk_off;
+  FastDiv fd_row;  // fact-row words + wd
+};
+constexpr int kJoinUnroll = 4;  // join-row words in flight per thread
+
+__device__ __forceinline__ uint32_t sorted_pair_key(const uint8_t* pairs, uint64_t p, uint32_t kb) {
+  const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(pairs + p * 16));
+  return __byte_perm(w, 0, 0x0123) >> (8 * (4 - kb));
+}
+
+template <int WB, int IPT, bool STAGE, bool VEC, bool JOIN = false>
 __global__ void __launch_bounds__(kTileThreads)
     k_unpart_runs(uint64_t n, uint32_t nb, uint32_t G, uint64_t per, const uint32_t* __restrict__ off,
                   const uint32_t* __restrict__ cur_g, const uint16_t* __restrict__ tpos,
                   const uint16_t* __restrict__ tcnt_g, const uint8_t* __restrict__ internal,
-                  uint8_t* __restrict__ dst, uint32_t W, FastDiv fdW, const int* err) {
+                  uint8_t* __restrict__ dst, uint32_t W, FastDiv fdW, int* err, JoinTail jt) {
   using Wd = typename WordT<WB>::T;
+  static_assert(!JOIN || (STAGE && !VEC), "join rows are staged word streams");
   constexpr uint32_t T = kTileThreads * IPT;
   extern __shared__ __align__(16) uint8_t sm[];
   __shared__ uint32_t wsum[32];
@@ -381,21 +392,24 @@ __global__ void __launch_bounds__(kTileThreads)
   uint32_t* toff = tcnt + nb;
   uint16_t* pos = reinterpret_cast<uint16_t*>(sm + (((size_t)nb * 12 + 15) & ~size_t(15)));  // tpos, or its inverse
   Wd* stage = reinterpret_cast<Wd*>(reinterpret_cast<uint8_t*>(pos) + 2 * T);
+  uint32_t* skey = reinterpret_cast<uint32_t*>(stage + (size_t)T * W);  // JOIN: key(t0 + j)
   const Wd* iw = reinterpret_cast<const Wd*>(internal);
   Wd* dw = reinterpret_cast<Wd*>(dst);
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool bad = false;
   // this thread owns runs x0 and x0 + 1: their cursors live in registers
   const uint32_t x0 = 2 * threadIdx.x;
   for (uint32_t g = blockIdx.x; g < G; g += gridDim.x) {
   uint32_t cur0 = x0 < nb ? off[x0] + cur_g[(uint64_t)g * nb + x0] : 0u;
   uint32_t cur1 = x0 + 1 < nb ? off[x0 + 1] + cur_g[(uint64_t)g * nb + x0 + 1] : 0u;
   const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
-  uint32_t tp[IPT], c0, c1;
+  uint32_t tp[IPT], kk[IPT], c0, c1;
   auto fetch = [&](uint64_t t0) {
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       const uint64_t i = t0 + k * kTileThreads + threadIdx.x;
       tp[k] = i < hi ? (uint32_t)tpos[i] : 0u;
+      if constexpr (JOIN) kk[k] = i < hi ? sorted_pair_key(jt.pairs, i, jt.kb) : 0u;
     }
     const uint16_t* tc = tcnt_g + (t0 / T) * nb;
     const bool in = t0 < hi;
@@ -411,6 +425,7 @@ __global__ void __launch_bounds__(kTileThreads)
       if (j < tn) {
         if (STAGE) pos[j] = (uint16_t)tp[k];
         else pos[tp[k]] = (uint16_t)j;
+        if constexpr (JOIN) skey[j] = kk[k];
       }
     }
     // exclusive scan of the tile's counts; cursors advance past the tile
@@ -465,7 +480,42 @@ __global__ void __launch_bounds__(kTileThreads)
       if constexpr (WB >= 4) cp_async_wait_all();
       __syncthreads();
       const uint32_t total = tn * W;
-      if constexpr (VEC) {
+      if constexpr (JOIN) {
+        const uint32_t row_w = W + jt.wd, rows_w = tn * row_w;
+        const uint32_t pk_w0 = jt.pk_off / WB, pk_w1 = (jt.pk_off + 8 + WB - 1) / WB;
+        const Wd* dimw = reinterpret_cast<const Wd*>(jt.dim);
+        Wd* o0 = dw + t0 * row_w;
+        // word u = row j, word w of the row, walked in steps of kTileThreads words
+        const uint32_t qs = (uint32_t)fdiv(kTileThreads, jt.fd_row), rs = kTileThreads - qs * row_w;
+        uint32_t j = (uint32_t)fdiv(threadIdx.x, jt.fd_row), w = threadIdx.x - j * row_w;
+        for (uint32_t t = threadIdx.x; t < rows_w; t += kTileThreads * kJoinUnroll) {
+          Wd x[kJoinUnroll];
+#pragma unroll
+          for (int k = 0; k < kJoinUnroll; ++k) {
+            const uint32_t u = t + k * kTileThreads;
+            if (u < rows_w) {
+              if (w < W) {
+                x[k] = stage[(uint32_t)pos[j] * W + w];
+              } else {
+                const uint32_t key = skey[j], wd = w - W;
+                x[k] = dimw[(uint64_t)key * jt.wd + wd];
+                if (wd >= pk_w0 && wd < pk_w1 && !pk_word_ok<WB>(x[k], wd, jt.pk_off, key)) bad = true;
+              }
+            }
+            j += qs;
+            w += rs;
+            if (w >= row_w) {
+              w -= row_w;
+              ++j;
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < kJoinUnroll; ++k) {
+            const uint32_t u = t + k * kTileThreads;
+            if (u < rows_w) o0[u] = x[k];
+          }
+        }
+      } else if constexpr (VEC) {
         // 16-byte chunk c = words [V*c, V*c + V) of the tile's destination
         constexpr uint32_t V = 16 / WB;
         const uint32_t C = total / V;
@@ -510,6 +560,7 @@ __global__ void __launch_bounds__(kTileThreads)
     __syncthreads();
   }
   }
+  if (JOIN && bad) atomicOr(err, ERR_RANGE);
 }
 
 
@@ -543,7 +594,11 @@ Layout4 layout4(const dpg_ctx& ctx, const Retrieval& r, const Plan& plan, bool s
   // Phase III: records of 96 bytes and more are gathered through a 4-byte
   // INTERNAL slot per rid (the 3-pass gather), so Phase I takes its largest
   // tile; smaller ones are rebuilt tile by tile from 2-byte tile places
-  L.slot_mode = r.join || env_int("DPG_L2_SLOT", r.rec >= 96 ? 1 : 0) != 0;  // join rows read through slots
+  // DPG-sort join rows are rebuilt like records where the fact rows can be
+  // staged (up to 128 bytes, the smallest tile's share); other join rows go
+  // through slots
+  const bool join_tiles = r.join && r.join->mode == 1 && r.rec <= 128;
+  L.slot_mode = env_int("DPG_L2_SLOT", r.join ? !join_tiles : r.rec >= 96) != 0 || (r.join && !join_tiles);
   part_tile(L.slot_mode ? 1 : r.rec, L.T, L.stage_mode);
   // CTA ranges: whole 4096-rid blocks (every tile starts at a multiple of T),
   // kL2Ranges per SM so that every resident count of 2, 3 or 4 CTAs per SM
@@ -582,7 +637,7 @@ void launch_unpart(dpg_ctx& ctx, const Layout4& L, uint64_t n, uint32_t rec, con
     set_smem(kern, smem);                                                                                      \
     const uint32_t grid = std::min<uint32_t>(L.G, ctx.sms * resident_per_sm(kern, kTileThreads, smem));        \
     kern<<<grid, kTileThreads, smem, st>>>(n, L.nb, L.G, L.per, off, cnt, tpos, tcnt, internal, dst, W, f,     \
-                                           ctx.d_err);                                                         \
+                                           ctx.d_err, JoinTail{});                                             \
   }
   if (!L.stage_mode) DPG_UNPART(4, false)
   else if (L.T == 4096) DPG_UNPART(8, true)
@@ -590,6 +645,33 @@ void launch_unpart(dpg_ctx& ctx, const Layout4& L, uint64_t n, uint32_t rec, con
   else if (L.T == 1024) DPG_UNPART(2, true)
   else DPG_UNPART(1, true)
 #undef DPG_UNPART
+}
+
+// Phase III of the DPG-sort join on this plan: k_unpart_runs<JOIN> writes
+// fact row || dimension row per tile entry (fact rows staged, see part_tile).
+template <int WB>
+void launch_unpart_join(dpg_ctx& ctx, const Layout4& L, const Retrieval& r, const uint32_t* off, const uint32_t* cnt,
+                        const uint16_t* tpos, const uint16_t* tcnt, const uint8_t* internal) {
+  const JoinSpec& j = *r.join;
+  const uint32_t W = r.rec / WB;
+  const FastDiv f = make_fastdiv(W);
+  const JoinTail jt{j.dim, j.sorted_pairs, j.dim_bytes / WB, j.key_bytes, j.pk_off,
+                    make_fastdiv(W + j.dim_bytes / WB)};
+  const size_t smem = (((size_t)L.nb * 12 + 15) & ~size_t(15)) + 2 * (size_t)L.T + (size_t)L.T * r.rec +
+                      4 * (size_t)L.T;
+#define DPG_UNPART_JOIN(IPTV)                                                                                 \
+  {                                                                                                           \
+    auto kern = k_unpart_runs<WB, IPTV, true, false, true>;                                                   \
+    set_smem(kern, smem);                                                                                     \
+    const uint32_t grid = std::min<uint32_t>(L.G, ctx.sms * resident_per_sm(kern, kTileThreads, smem));       \
+    kern<<<grid, kTileThreads, smem, r.stream>>>(r.n, L.nb, L.G, L.per, off, cnt, tpos, tcnt, internal, j.out, \
+                                                 W, f, ctx.d_err, jt);                                        \
+  }
+  if (L.T == 4096) DPG_UNPART_JOIN(8)
+  else if (L.T == 2048) DPG_UNPART_JOIN(4)
+  else if (L.T == 1024) DPG_UNPART_JOIN(2)
+  else DPG_UNPART_JOIN(1)
+#undef DPG_UNPART_JOIN
 }
 
 template <class Rid>
@@ -676,7 +758,20 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
     ctx.launches++;
   }
   // Phase III
-  if (r.join) {
+  if (r.join && !L.slot_mode) {
+    TraceScope ts(ctx, "k_unpart_join", r.stream);
+    const JoinSpec& j = *r.join;
+    const uint32_t wb3 = std::min({pow2_align(r.rec), pow2_align(j.dim_bytes), pow2_align(reinterpret_cast<uintptr_t>(j.out)),
+                                   pow2_align(reinterpret_cast<uintptr_t>(j.dim))});
+    switch (wb3) {
+      case 16: launch_unpart_join<16>(ctx, L, r, off, cnt, tpos, tcnt, stage); break;
+      case 8: launch_unpart_join<8>(ctx, L, r, off, cnt, tpos, tcnt, stage); break;
+      case 4: launch_unpart_join<4>(ctx, L, r, off, cnt, tpos, tcnt, stage); break;
+      case 2: launch_unpart_join<2>(ctx, L, r, off, cnt, tpos, tcnt, stage); break;
+      default: launch_unpart_join<1>(ctx, L, r, off, cnt, tpos, tcnt, stage); break;
+    }
+    ctx.launches++;
+  } else if (r.join) {
     launch_join_phase3(ctx, r, stage, slot);
   } else if (L.slot_mode) {
     const uint32_t wb3 = std::min(pow2_align(r.rec), pow2_align(reinterpret_cast<uintptr_t>(r.dst)));

@@ -61,30 +61,52 @@ def test_join_matches_oracle(ctx, n_dim, n_fact, s):
 @pytest.mark.parametrize("variant", ["2", "3", "4"])
 def test_join_retrieval_plans(ctx, monkeypatch, variant, run_kb):
     """The same join rows whatever retrieval plan is set: the L2-run plan
-    (Phase III through INTERNAL slots, the DPG-move key check in Phase II),
-    the 3-pass plan, and the 2-pass plan, which falls back to the 3-pass plan
-    because join rows need INTERNAL."""
+    (DPG-move rows through INTERNAL slots with the key check in Phase II,
+    DPG-sort rows rebuilt tile by tile), the 3-pass plan, and the 2-pass
+    plan, which falls back to the 3-pass plan because join rows need
+    INTERNAL."""
     monkeypatch.setenv("DPG_VARIANT", variant)
     monkeypatch.setenv("DPG_L2_RUN_KB", run_kb)
     dim, fact, fk = synth.fk_tables(5000, 200_000, 64, 16, 0.8, 9)
     run_all(ctx, dim, fact)
 
 
+@pytest.mark.parametrize("slot", ["0", "1"])
+def test_join_sort_phase3_paths(ctx, monkeypatch, slot):
+    """DPG-sort join rows on the L2-run plan, both Phase III paths: fact rows
+    of up to 128 bytes rebuilt tile by tile with their dimension rows
+    appended, larger ones (and all with DPG_L2_SLOT=1) gathered through
+    INTERNAL slots; every layout against the oracle, a ragged last tile."""
+    monkeypatch.setenv("DPG_VARIANT", "4")
+    monkeypatch.setenv("DPG_L2_SLOT", slot)
+    dim, fact, fk = synth.fk_tables(3000, 100_003, 64, 16, 0.8, 21)
+    for fb, fo, db, po in ((16, 0, 64, 0), (24, 8, 40, 16), (12, 4, 20, 12), (128, 0, 64, 0), (132, 4, 64, 0),
+                           (4, 0, 8, 0), (16, 12, 100, 3), (20, 0, 9, 1)):
+        d, f = relayout(dim, fact, fk, fb, fo, db, po)
+        want = oracle.fk_join_sorted(f, d, fo, po)
+        out = ctx.fk_join(to_dev(f), to_dev(d), "sort", fo, po)
+        ctx.sync()
+        assert np.array_equal(out.cpu().numpy(), want), (fb, fo, db, po)
+
+
+@pytest.mark.parametrize("mode", ["move", "sort"])
 @pytest.mark.parametrize("variant", ["3", "4"])
-def test_join_bad_keys_each_plan(ctx, monkeypatch, variant):
-    """A referenced dimension row whose key is not its row number: DPG-move
-    reports it before writing any output row, on either plan."""
+def test_join_bad_keys_each_plan(ctx, monkeypatch, variant, mode):
+    """A referenced dimension row whose key is not its row number, one byte
+    off at several places of the key: reported on either plan; DPG-move
+    reports it before writing any output row."""
     from paper_cs_0308004_gb300 import dpg
     monkeypatch.setenv("DPG_VARIANT", variant)
     dim, fact, fk = synth.fk_tables(3000, 80_000, 64, 16, 0.8, 12)
-    for pk_off, dim_bytes in ((0, 64), (3, 100), (56, 64)):
+    for pk_off, dim_bytes, flip in ((0, 64, 2), (3, 100, 2), (56, 64, 2), (0, 64, 7), (3, 100, 5), (8, 40, 0)):
         d, f = relayout(dim, fact, fk, 16, 0, dim_bytes, pk_off)
-        d[int(fk[123]), pk_off + 2] ^= 0x40                              # one byte of one referenced key
+        d[int(fk[123]), pk_off + flip] ^= 0x40                           # one byte of one referenced key
         out = torch.full((80_000, 16 + dim_bytes), 0x33, dtype=torch.uint8, device=DEV)
-        ctx.fk_join(to_dev(f), to_dev(d), "move", 0, pk_off, out=out)
+        ctx.fk_join(to_dev(f), to_dev(d), mode, 0, pk_off, out=out)
         with pytest.raises(dpg.DpgRangeError):
             ctx.sync()
-        assert bool((out == 0x33).all())
+        if mode == "move":
+            assert bool((out == 0x33).all())
 
 
 @pytest.mark.parametrize("fact_bytes,fk_off,dim_bytes,pk_off", [(24, 8, 40, 16), (4, 0, 8, 0), (12, 4, 20, 12),

@@ -356,27 +356,23 @@ __global__ void __launch_bounds__(kRunsGatherThreads, kProbeRunsMinCtas)
 // Without STAGE (large records) each sorted entry is copied straight to its
 // destination record through the inverse of tpos.
 // JOIN (DPG-sort join rows, §4.2.1): the destination row of tile entry j is
-// the staged fact row || dimension row key(p), p = t0 + j, key(p) the
-// big-endian bytes [0, kb) of sorted pair p (staged beside the records); the
-// int64 little-endian key at byte pk_off of that dimension row must equal
-// key(p), else the range bit.  Rows are written as one word stream.
+// the staged fact row || dimension row fk, fk the int32 at byte fk_off of
+// that staged fact row (the key it was sorted by); the int64 little-endian
+// key at byte pk_off of the dimension row must equal fk, else the range bit.
+// Rows are written as one word stream.
 struct JoinTail {
   const uint8_t* dim;
-  const uint8_t* pairs;
   uint32_t wd;  // dimension-row words
-  uint32_t kb;
+  uint32_t fk_off;
   uint32_t pk_off;
   FastDiv fd_row;  // fact-row words + wd
 };
-constexpr int kJoinUnroll = 4;  // join-row words in flight per thread
-
-__device__ __forceinline__ uint32_t sorted_pair_key(const uint8_t* pairs, uint64_t p, uint32_t kb) {
-  const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(pairs + p * 16));
-  return __byte_perm(w, 0, 0x0123) >> (8 * (4 - kb));
-}
+// join-row words in flight per thread; the join tile runs two CTAs per SM
+// (64 registers; unbounded it takes 80 and one CTA)
+constexpr int kJoinUnroll = 4;
 
 template <int WB, int IPT, bool STAGE, bool VEC, bool JOIN = false>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, JOIN ? 2 : 1)
     k_unpart_runs(uint64_t n, uint32_t nb, uint32_t G, uint64_t per, const uint32_t* __restrict__ off,
                   const uint32_t* __restrict__ cur_g, const uint16_t* __restrict__ tpos,
                   const uint16_t* __restrict__ tcnt_g, const uint8_t* __restrict__ internal,
@@ -392,7 +388,6 @@ __global__ void __launch_bounds__(kTileThreads)
   uint32_t* toff = tcnt + nb;
   uint16_t* pos = reinterpret_cast<uint16_t*>(sm + (((size_t)nb * 12 + 15) & ~size_t(15)));  // tpos, or its inverse
   Wd* stage = reinterpret_cast<Wd*>(reinterpret_cast<uint8_t*>(pos) + 2 * T);
-  uint32_t* skey = reinterpret_cast<uint32_t*>(stage + (size_t)T * W);  // JOIN: key(t0 + j)
   const Wd* iw = reinterpret_cast<const Wd*>(internal);
   Wd* dw = reinterpret_cast<Wd*>(dst);
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -403,13 +398,12 @@ __global__ void __launch_bounds__(kTileThreads)
   uint32_t cur0 = x0 < nb ? off[x0] + cur_g[(uint64_t)g * nb + x0] : 0u;
   uint32_t cur1 = x0 + 1 < nb ? off[x0 + 1] + cur_g[(uint64_t)g * nb + x0 + 1] : 0u;
   const uint64_t lo = (uint64_t)g * per, hi = min(n, lo + per);
-  uint32_t tp[IPT], kk[IPT], c0, c1;
+  uint32_t tp[IPT], c0, c1;
   auto fetch = [&](uint64_t t0) {
 #pragma unroll
     for (int k = 0; k < IPT; ++k) {
       const uint64_t i = t0 + k * kTileThreads + threadIdx.x;
       tp[k] = i < hi ? (uint32_t)tpos[i] : 0u;
-      if constexpr (JOIN) kk[k] = i < hi ? sorted_pair_key(jt.pairs, i, jt.kb) : 0u;
     }
     const uint16_t* tc = tcnt_g + (t0 / T) * nb;
     const bool in = t0 < hi;
@@ -425,7 +419,6 @@ __global__ void __launch_bounds__(kTileThreads)
       if (j < tn) {
         if (STAGE) pos[j] = (uint16_t)tp[k];
         else pos[tp[k]] = (uint16_t)j;
-        if constexpr (JOIN) skey[j] = kk[k];
       }
     }
     // exclusive scan of the tile's counts; cursors advance past the tile
@@ -484,6 +477,7 @@ __global__ void __launch_bounds__(kTileThreads)
         const uint32_t row_w = W + jt.wd, rows_w = tn * row_w;
         const uint32_t pk_w0 = jt.pk_off / WB, pk_w1 = (jt.pk_off + 8 + WB - 1) / WB;
         const Wd* dimw = reinterpret_cast<const Wd*>(jt.dim);
+        const uint8_t* sfk = reinterpret_cast<const uint8_t*>(stage) + jt.fk_off;  // fk_off % 4 == 0
         Wd* o0 = dw + t0 * row_w;
         // word u = row j, word w of the row, walked in steps of kTileThreads words
         const uint32_t qs = (uint32_t)fdiv(kTileThreads, jt.fd_row), rs = kTileThreads - qs * row_w;
@@ -497,7 +491,8 @@ __global__ void __launch_bounds__(kTileThreads)
               if (w < W) {
                 x[k] = stage[(uint32_t)pos[j] * W + w];
               } else {
-                const uint32_t key = skey[j], wd = w - W;
+                const uint32_t key = *reinterpret_cast<const uint32_t*>(sfk + (uint32_t)pos[j] * (W * WB));
+                const uint32_t wd = w - W;
                 x[k] = dimw[(uint64_t)key * jt.wd + wd];
                 if (wd >= pk_w0 && wd < pk_w1 && !pk_word_ok<WB>(x[k], wd, jt.pk_off, key)) bad = true;
               }
@@ -648,17 +643,16 @@ void launch_unpart(dpg_ctx& ctx, const Layout4& L, uint64_t n, uint32_t rec, con
 }
 
 // Phase III of the DPG-sort join on this plan: k_unpart_runs<JOIN> writes
-// fact row || dimension row per tile entry (fact rows staged, see part_tile).
+// fact row || dimension row per tile entry (fact rows staged, see part_tile;
+// the dimension row is the one the staged row's foreign key names).
 template <int WB>
 void launch_unpart_join(dpg_ctx& ctx, const Layout4& L, const Retrieval& r, const uint32_t* off, const uint32_t* cnt,
                         const uint16_t* tpos, const uint16_t* tcnt, const uint8_t* internal) {
   const JoinSpec& j = *r.join;
   const uint32_t W = r.rec / WB;
   const FastDiv f = make_fastdiv(W);
-  const JoinTail jt{j.dim, j.sorted_pairs, j.dim_bytes / WB, j.key_bytes, j.pk_off,
-                    make_fastdiv(W + j.dim_bytes / WB)};
-  const size_t smem = (((size_t)L.nb * 12 + 15) & ~size_t(15)) + 2 * (size_t)L.T + (size_t)L.T * r.rec +
-                      4 * (size_t)L.T;
+  const JoinTail jt{j.dim, j.dim_bytes / WB, j.fk_off, j.pk_off, make_fastdiv(W + j.dim_bytes / WB)};
+  const size_t smem = (((size_t)L.nb * 12 + 15) & ~size_t(15)) + 2 * (size_t)L.T + (size_t)L.T * r.rec;
 #define DPG_UNPART_JOIN(IPTV)                                                                                 \
   {                                                                                                           \
     auto kern = k_unpart_runs<WB, IPTV, true, false, true>;                                                   \

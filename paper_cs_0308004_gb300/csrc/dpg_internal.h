@@ -79,9 +79,12 @@ struct RidSpec {
 //          out row i = fact[i] || INTERNAL[slot[i]].  Phase II checks that
 //          each probed dimension row's key equals its row number.
 //   mode 1 (DPG-sort): the retrieval moves fact rows into the order of the
-//          (fk, fact row) pairs sorted by fk; out row j = INTERNAL[slot[j]] ||
-//          dim[fk_j], fk_j decoded from sorted pair j (key bytes [0, key_bytes)
-//          hold fk big-endian), the key of dim[fk_j] checked as it is copied.
+//          8-byte (fk, fact row) pairs sorted by fk; out row j = fact row j
+//          of that order || dim[fk_j], the key of dim[fk_j] checked as it is
+//          copied.  On the L2-run plan (fact rows up to 128 bytes) Phase III
+//          rebuilds tiles of fact rows and reads fk_j from the staged row;
+//          otherwise it reads INTERNAL[slot[j]] and decodes fk_j from sorted
+//          pair j (key bytes [0, key_bytes) hold fk big-endian).
 struct JoinSpec {
   int mode;
   const uint8_t* fact;
@@ -153,9 +156,12 @@ int run_join_direct(dpg_ctx& ctx, const JoinSpec& j, uint64_t n_fact, cudaStream
 
 // Stable LSD radix sort of 16-byte pairs on key bytes [0, key_bytes) (dpg_sort.cu).
 // `a` holds the pairs; the result ends in `a` (even key_bytes) or `b`; the
-// returned pointer says which.
+// returned pointer says which.  run_radix_pairs8: the same for 8-byte pairs
+// (key bytes [0, key_bytes <= 4) in the first word, the rid in the second).
 uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
                          cudaStream_t st, int* status);
+uint8_t* run_radix_pairs8(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
+                          cudaStream_t st, int* status);
 
 // Phases 1-2 of the §3 sort (dpg_sort.cu): sorted 16-byte key-pointer pairs.
 size_t sort_scan_bytes(uint64_t n);

@@ -8,8 +8,8 @@
 //
 //   DPG-move: move F's rows into R's order by DPG retrieval with the fk column
 //             as the rid sequence; Phase III writes fact[i] || dim[fk_i].
-//   DPG-sort: sort the rid pairs (rid_F, rid_R) by rid_F (stable radix sort on
-//             the low bytes of fk), then move R's rows into that order by DPG
+//   DPG-sort: sort the rid pairs (rid_F, rid_R) by rid_F (stable radix sort of
+//             8-byte pairs on the low bytes of fk), then move R's rows into that order by DPG
 //             retrieval; Phase III writes fact row || dim[fk].
 //   direct:   out[i] = fact[i] || dim[fk_i] in one pass (baseline).
 #include <algorithm>
@@ -20,21 +20,19 @@
 namespace dpg {
 namespace {
 
-// Pair i of the DPG-sort join: key bytes [0, kb) = fk big-endian, rid = i.
-// A foreign key outside [0, n_dim) raises the range bit.
+// Pair i of the DPG-sort join (8 bytes): key bytes [0, kb) = fk big-endian
+// in the first word, rid = i in the second.  A foreign key outside
+// [0, n_dim) raises the range bit.
 __global__ void __launch_bounds__(256)
     k_extract_fk_pairs(const uint8_t* __restrict__ fact, uint64_t n, uint32_t fact_bytes, uint32_t fk_off,
-                       uint64_t n_dim, uint32_t kb, uint4* __restrict__ pairs, int* err) {
+                       uint64_t n_dim, uint32_t kb, uint2* __restrict__ pairs, int* err) {
   bool bad = false;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t fk = (uint32_t)__ldg(reinterpret_cast<const int32_t*>(fact + i * fact_bytes + fk_off));
     if ((uint64_t)fk >= n_dim) bad = true;
-    uint32_t w[4] = {0u, 0u, 0u, (uint32_t)i};
-    for (uint32_t j = 0; j < kb; ++j) {
-      const uint32_t byte = (fk >> (8 * (kb - 1 - j))) & 0xffu;
-      w[j >> 2] |= byte << (8 * (j & 3));
-    }
-    pairs[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    uint32_t key = 0;
+    for (uint32_t j = 0; j < kb; ++j) key |= ((fk >> (8 * (kb - 1 - j))) & 0xffu) << (8 * j);
+    pairs[i] = make_uint2(key, (uint32_t)i);
   }
   if (bad) atomicOr(err, ERR_RANGE);
 }
@@ -97,22 +95,22 @@ extern "C" dpg_status dpg_fk_join(dpg_ctx* c, const void* fact_v, size_t n_fact,
   uint32_t kb = 1;
   while (kb < 4 && n_dim > (1ull << (8 * kb))) ++kb;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t bp = al(n_fact * 16), bs = sort_scan_bytes(n_fact);
+  const size_t bp = al(n_fact * 8), bs = sort_scan_bytes(n_fact);
   if (int s = ensure_aux(*c, 2 * bp + bs)) return (dpg_status)s;
   uint8_t* a = static_cast<uint8_t*>(c->aux);
   {
     TraceScope ts(*c, "k_extract_fk_pairs", st);
     const int grid = (int)std::min<uint64_t>((n_fact + 255) / 256, (uint64_t)c->sms * 8);
     k_extract_fk_pairs<<<grid, 256, 0, st>>>(fact, n_fact, (uint32_t)fact_bytes, (uint32_t)fk_off, n_dim, kb,
-                                             reinterpret_cast<uint4*>(a), c->d_err);
+                                             reinterpret_cast<uint2*>(a), c->d_err);
     c->launches++;
   }
   int status = DPG_OK;
-  uint8_t* sorted = run_radix_pairs(*c, a, a + bp, a + 2 * bp, n_fact, kb, st, &status);
+  uint8_t* sorted = run_radix_pairs8(*c, a, a + bp, a + 2 * bp, n_fact, kb, st, &status);
   if (status != DPG_OK) return (dpg_status)status;
   j.sorted_pairs = sorted;
   j.key_bytes = kb;
-  Retrieval r{fact, n_fact, (uint32_t)fact_bytes, n_fact, RidSpec{sorted + 12, 16}, out, st};
+  Retrieval r{fact, n_fact, (uint32_t)fact_bytes, n_fact, RidSpec{sorted + 4, 8}, out, st};
   r.join = &j;
   return (dpg_status)run_dpg(*c, r, choose_plan(*c, r));
 }

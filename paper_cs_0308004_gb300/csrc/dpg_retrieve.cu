@@ -447,11 +447,11 @@ struct RowField {  // int32 field of strided rows (a foreign-key column)
     return (uint64_t)(uint32_t)__ldg(reinterpret_cast<const int32_t*>(base + r * stride));
   }
 };
-struct RowPairKey {  // big-endian key bytes [0, kb) of sorted 16-byte pair r (kb <= 4)
+struct RowPairKey {  // big-endian key bytes [0, kb) of sorted 8-byte pair r (kb <= 4)
   const uint8_t* pairs;
   uint32_t kb;
   __device__ __forceinline__ uint64_t operator()(uint64_t r) const {
-    const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(pairs + r * 16));
+    const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(pairs + r * 8));
     return (uint64_t)(__byte_perm(w, 0, 0x0123) >> (8 * (4 - kb)));
   }
 };

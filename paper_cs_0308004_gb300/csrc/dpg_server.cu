@@ -92,10 +92,10 @@ int footprint(dpg_server& s, const dpg_job& j, size_t* work, size_t* out, size_t
       dpg::JoinSpec js{};
       js.mode = 1;
       dpg::Retrieval r{static_cast<const uint8_t*>(j.fact), j.n_fact, (uint32_t)j.fact_bytes, j.n_fact,
-                       dpg::RidSpec{nullptr, 16}, nullptr, nullptr};
+                       dpg::RidSpec{nullptr, 8}, nullptr, nullptr};
       r.join = &js;
       scratch = dpg::retrieve_scratch_need(c, r);
-      aux = 2 * al256(j.n_fact * 16) + dpg::sort_scan_bytes(j.n_fact);
+      aux = 2 * al256(j.n_fact * 8) + dpg::sort_scan_bytes(j.n_fact);
     }
     *scratch_part = al256(scratch);
     *work = *scratch_part + al256(aux);

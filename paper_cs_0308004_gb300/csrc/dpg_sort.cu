@@ -63,19 +63,25 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Key byte `byte` of a pair: 16-byte pairs hold up to 12 key bytes in words
+// x, y, z; 8-byte pairs (the DPG-sort join's) up to 4 in x, the rid in y.
 __device__ __forceinline__ uint32_t pair_digit(const uint4& p, uint32_t byte) {
   const uint32_t word = byte < 4 ? p.x : (byte < 8 ? p.y : p.z);
   return (word >> (8 * (byte & 3))) & 0xffu;
 }
+__device__ __forceinline__ uint32_t pair_digit(const uint2& p, uint32_t byte) {
+  return (p.x >> (8 * (byte & 3))) & 0xffu;
+}
 
 // Digit counts of every key byte over all pairs: counts[j * 256 + d].
+template <class E>
 __global__ void __launch_bounds__(1024)
-    k_rs_global_hist(const uint4* __restrict__ in, uint64_t n, uint32_t key_bytes, uint32_t* __restrict__ counts) {
+    k_rs_global_hist(const E* __restrict__ in, uint64_t n, uint32_t key_bytes, uint32_t* __restrict__ counts) {
   __shared__ uint32_t h[12 * 256];
   for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x) h[x] = 0;
   __syncthreads();
   for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x) {
-    const uint4 v = in[e];
+    const E v = in[e];
     for (uint32_t j = 0; j < key_bytes; ++j) atomicAdd(&h[j * 256 + pair_digit(v, j)], 1u);
   }
   __syncthreads();
@@ -87,14 +93,17 @@ constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kCountMask = (1u
 
 // One stable pass on key byte `byte`.  Tiles are numbered in the order CTAs
 // start (tile_ctr), so a tile only waits for tiles whose CTAs already run.
+// E: uint4 (16-byte pairs) or uint2 (8-byte pairs).
+template <class E>
 __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
-    k_rs_onesweep(const uint4* __restrict__ in, uint4* __restrict__ out, uint64_t n, uint32_t byte,
+    k_rs_onesweep(const E* __restrict__ in, E* __restrict__ out, uint64_t n, uint32_t byte,
                   const uint32_t* __restrict__ digit_count, uint32_t* status, uint32_t* tile_ctr, int* err) {
   __shared__ uint16_t whist[kRsWarps][256];
   __shared__ uint32_t wmask[kRsWarps][256];  // lanes of a warp holding digit d in this round
   __shared__ uint32_t tcnt[256], toff[256], s_base[256], s_excl[256];
   __shared__ uint32_t s_tile;
-  extern __shared__ uint4 sbuf[];                              // kRsTile pairs
+  extern __shared__ uint4 sraw[];
+  E* sbuf = reinterpret_cast<E*>(sraw);                        // kRsTile pairs
   uint8_t* sdig = reinterpret_cast<uint8_t*>(sbuf + kRsTile);  // kRsTile digits
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
@@ -127,7 +136,7 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
       run += c[j];
     }
   }
-  uint4 v[kRsItems];
+  E v[kRsItems];
   uint32_t d[kRsItems], rank[kRsItems];
   // all of the tile's loads first: the ranking below has warp barriers,
   // which would otherwise hold each load back until the previous round ends
@@ -240,13 +249,16 @@ size_t sort_scan_bytes(uint64_t n) {
   return ((256 * ntiles * 4 + 255) & ~255ull) + 16384;
 }
 
-uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint64_t n, uint32_t key_bytes,
-                         cudaStream_t st, int* status) {
+namespace {
+
+template <class E>
+uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint64_t n, uint32_t key_bytes,
+                     cudaStream_t st, int* status) {
   *status = DPG_OK;
-  uint4* a = reinterpret_cast<uint4*>(a_);
-  uint4* b = reinterpret_cast<uint4*>(b_);
+  E* a = reinterpret_cast<E*>(a_);
+  E* b = reinterpret_cast<E*>(b_);
   if (n == 0) return a_;
-  if (n > kCountMask) {
+  if (n > kCountMask || key_bytes > (sizeof(E) == 16 ? 12u : 4u)) {
     *status = DPG_EINVAL;
     return nullptr;
   }
@@ -263,11 +275,11 @@ uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, 
   {
     TraceScope ts(ctx, "k_rs_global_hist", st);
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 1023) / 1024, (uint64_t)ctx.sms * 2));
-    k_rs_global_hist<<<grid, 1024, 0, st>>>(a, n, key_bytes, counts);
+    k_rs_global_hist<E><<<grid, 1024, 0, st>>>(a, n, key_bytes, counts);
     ctx.launches++;
   }
-  const size_t smem = kRsTile * (sizeof(uint4) + 1);
-  cudaFuncSetAttribute(k_rs_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = kRsTile * (sizeof(E) + 1);
+  cudaFuncSetAttribute(k_rs_onesweep<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (int byte = (int)key_bytes - 1; byte >= 0; --byte) {
     e = cudaMemsetAsync(tile_status, 0, (size_t)ntiles * 256 * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, 4, st);
@@ -277,8 +289,8 @@ uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, 
     }
     {
       TraceScope ts(ctx, "k_rs_onesweep", st);
-      k_rs_onesweep<<<ntiles, kRsThreads, smem, st>>>(a, b, n, (uint32_t)byte, counts + 256 * byte, tile_status,
-                                                     tile_ctr, ctx.d_err);
+      k_rs_onesweep<E><<<ntiles, kRsThreads, smem, st>>>(a, b, n, (uint32_t)byte, counts + 256 * byte, tile_status,
+                                                        tile_ctr, ctx.d_err);
     }
     ctx.launches++;
     std::swap(a, b);
@@ -286,6 +298,18 @@ uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, 
   e = cudaGetLastError();
   if (e != cudaSuccess) *status = cuda_fail(ctx, e, "sort launch");
   return reinterpret_cast<uint8_t*>(a);
+}
+
+}  // namespace
+
+uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
+                         cudaStream_t st, int* status) {
+  return radix_pairs<uint4>(ctx, a, b, scan, n, key_bytes, st, status);
+}
+
+uint8_t* run_radix_pairs8(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
+                          cudaStream_t st, int* status) {
+  return radix_pairs<uint2>(ctx, a, b, scan, n, key_bytes, st, status);
 }
 
 int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, uint32_t key_bytes, uint8_t* pairs,

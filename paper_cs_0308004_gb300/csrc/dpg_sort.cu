@@ -10,7 +10,7 @@
 // per pass (byte key_bytes-1 first, byte 0 last).  k_rs_global_hist counts
 // every key byte's digits over all pairs once (the counts do not depend on
 // the order).  Each pass is then one kernel, k_rs_onesweep: a CTA takes the
-// next tile of kRsTile pairs, ranks them stably (per-warp digit counts, the
+// next tile (64 KB of pairs), ranks them stably (per-warp digit counts, the
 // lanes sharing a digit found with a shared-memory OR, prefix over warps),
 // publishes its digit counts, and
 // finds how many pairs of each digit earlier tiles hold by looking back over
@@ -25,14 +25,15 @@
 namespace dpg {
 namespace {
 
-// 4096-pair tiles, two CTAs per SM: half as many tiles as 2048-pair tiles
-// at three per SM, so half as many look-back walks and block barriers per
-// byte (109 against 138 us per pass over 1e7 pairs).
+// Tiles of 4096 16-byte or 8192 8-byte pairs (64 KB), two CTAs per SM: the
+// fewer tiles per byte, the fewer look-back walks and block barriers (4096
+// 16-byte pairs: 109 against 138 us per pass over 1e7 pairs for 2048 at three
+// CTAs per SM).
 constexpr int kRsThreads = 512;
-constexpr int kRsItems = 8;
 constexpr int kRsMinBlocks = 2;
-constexpr uint32_t kRsTile = kRsThreads * kRsItems;  // pairs per tile
 constexpr int kRsWarps = kRsThreads / 32;
+template <class E> __host__ __device__ constexpr int rs_items() { return sizeof(E) == 16 ? 8 : 16; }
+template <class E> __host__ __device__ constexpr uint32_t rs_tile() { return kRsThreads * rs_items<E>(); }  // pairs per tile
 
 // Phase 1: pairs[i] = (key of record i, zero pad, i).  WORDS: records and
 // the table are 4-byte aligned, so the key is read as ceil(key_bytes/4)
@@ -102,9 +103,11 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
   __shared__ uint32_t wmask[kRsWarps][256];  // lanes of a warp holding digit d in this round
   __shared__ uint32_t tcnt[256], toff[256], s_base[256], s_excl[256];
   __shared__ uint32_t s_tile;
+  constexpr int kItems = rs_items<E>();
+  constexpr uint32_t kTile = rs_tile<E>();
   extern __shared__ uint4 sraw[];
-  E* sbuf = reinterpret_cast<E*>(sraw);                        // kRsTile pairs
-  uint8_t* sdig = reinterpret_cast<uint8_t*>(sbuf + kRsTile);  // kRsTile digits
+  E* sbuf = reinterpret_cast<E*>(sraw);                      // kTile pairs
+  uint8_t* sdig = reinterpret_cast<uint8_t*>(sbuf + kTile);  // kTile digits
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
   }
   __syncthreads();
   const uint32_t t = s_tile;
-  const uint64_t base = (uint64_t)t * kRsTile;
+  const uint64_t base = (uint64_t)t * kTile;
   // digit bases of this pass: exclusive scan of the digit counts (warp 1, 8 per lane)
   if (warp == 1) {
     uint32_t c[8], sum = 0;
@@ -136,32 +139,32 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
       run += c[j];
     }
   }
-  E v[kRsItems];
-  uint32_t d[kRsItems], rank[kRsItems];
+  // this thread's pairs: kItems rounds of 32 consecutive pairs of its warp
+  // (the digit is recomputed from the pair where it is needed)
+  const uint64_t e0 = base + (uint64_t)warp * (32 * kItems) + lane;
+  E v[kItems];
+  uint32_t rank[kItems];
   // all of the tile's loads first: the ranking below has warp barriers,
   // which would otherwise hold each load back until the previous round ends
 #pragma unroll
-  for (int k = 0; k < kRsItems; ++k) {
-    const uint64_t e = base + (uint64_t)warp * (32 * kRsItems) + (uint64_t)k * 32 + lane;
-    if (e < n) v[k] = in[e];
-  }
+  for (int k = 0; k < kItems; ++k)
+    if (e0 + (uint64_t)k * 32 < n) v[k] = in[e0 + (uint64_t)k * 32];
 #pragma unroll
-  for (int k = 0; k < kRsItems; ++k) {
-    const uint64_t e = base + (uint64_t)warp * (32 * kRsItems) + (uint64_t)k * 32 + lane;
-    const bool ok = e < n;
-    d[k] = ok ? pair_digit(v[k], byte) : 256u + lane;  // unique sentinel per lane past the end
+  for (int k = 0; k < kItems; ++k) {
+    const bool ok = e0 + (uint64_t)k * 32 < n;
+    const uint32_t d = ok ? pair_digit(v[k], byte) : 0u;
     // peers: the lanes of this warp with the same digit, gathered by a
     // shared-memory OR (cheaper here than __match_any_sync)
-    if (ok) atomicOr(&wmask[warp][d[k]], 1u << lane);
+    if (ok) atomicOr(&wmask[warp][d], 1u << lane);
     __syncwarp();
-    const uint32_t peers = ok ? wmask[warp][d[k]] : (1u << lane);
+    const uint32_t peers = ok ? wmask[warp][d] : (1u << lane);
     const uint32_t before = __popc(peers & lt);
     uint32_t prior = 0;
-    if (ok) prior = whist[warp][d[k]];
+    if (ok) prior = whist[warp][d];
     __syncwarp();
     if (ok && before == 0) {
-      whist[warp][d[k]] = (uint16_t)(prior + __popc(peers));
-      wmask[warp][d[k]] = 0;
+      whist[warp][d] = (uint16_t)(prior + __popc(peers));
+      wmask[warp][d] = 0;
     }
     __syncwarp();
     rank[k] = prior + before;
@@ -224,15 +227,16 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < kRsItems; ++k) {
-    if (d[k] < 256u) {
-      const uint32_t p = toff[d[k]] + whist[warp][d[k]] + rank[k];
+  for (int k = 0; k < kItems; ++k) {
+    if (e0 + (uint64_t)k * 32 < n) {
+      const uint32_t d = pair_digit(v[k], byte);
+      const uint32_t p = toff[d] + whist[warp][d] + rank[k];
       sbuf[p] = v[k];
-      sdig[p] = (uint8_t)d[k];
+      sdig[p] = (uint8_t)d;
     }
   }
   __syncthreads();
-  const uint32_t tn = (uint32_t)((n - base) < kRsTile ? (n - base) : kRsTile);
+  const uint32_t tn = (uint32_t)((n - base) < kTile ? (n - base) : kTile);
   for (uint32_t p = threadIdx.x; p < tn; p += kRsThreads) {
     const uint32_t dg = sdig[p];
     out[(uint64_t)s_base[dg] + s_excl[dg] + (p - toff[dg])] = sbuf[p];
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
 // (n_src x 16 bytes).  `tmp` is n_src x 16 bytes of scratch; `scan` holds the
 // count matrix and scan buffers (see sort_scan_bytes).
 size_t sort_scan_bytes(uint64_t n) {
-  const uint64_t ntiles = (n + kRsTile - 1) / kRsTile;
+  const uint64_t ntiles = (n + rs_tile<uint4>() - 1) / rs_tile<uint4>();  // the smaller tile: the most tiles
   return ((256 * ntiles * 4 + 255) & ~255ull) + 16384;
 }
 
@@ -262,7 +266,7 @@ uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint
     *status = DPG_EINVAL;
     return nullptr;
   }
-  const uint32_t ntiles = (uint32_t)((n + kRsTile - 1) / kRsTile);
+  const uint32_t ntiles = (uint32_t)((n + rs_tile<E>() - 1) / rs_tile<E>());
   uint32_t* tile_status = reinterpret_cast<uint32_t*>(scan);
   uint8_t* rest = scan + ((256ull * ntiles * 4 + 255) & ~255ull);
   uint32_t* counts = reinterpret_cast<uint32_t*>(rest);  // key_bytes x 256
@@ -278,7 +282,7 @@ uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint
     k_rs_global_hist<E><<<grid, 1024, 0, st>>>(a, n, key_bytes, counts);
     ctx.launches++;
   }
-  const size_t smem = kRsTile * (sizeof(E) + 1);
+  const size_t smem = rs_tile<E>() * (sizeof(E) + 1);
   cudaFuncSetAttribute(k_rs_onesweep<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (int byte = (int)key_bytes - 1; byte >= 0; --byte) {
     e = cudaMemsetAsync(tile_status, 0, (size_t)ntiles * 256 * 4, st);

@@ -456,8 +456,14 @@ struct RowPairKey {  // big-endian key bytes [0, kb) of sorted 8-byte pair r (kb
   }
 };
 
-template <int WB, class IA, class IB, bool CHECK_B>
-__global__ void __launch_bounds__(kGatherThreads)
+// U words per thread per step; MINB CTAs per SM asked of the compiler (0:
+// none; its own choice is 53 registers and four CTAs at U = 8).  Measured
+// on the 2e8-row join: DPG-move rows (key = an INTERNAL slot) 6.84 ms at
+// U = 8 unbounded against 7.80 ms at U = 4 with eight CTAs per SM; direct
+// rows (key = the fact row's fk, then a random dimension row) 6.31 ms at
+// U = 4 with eight CTAs per SM against 8.94 ms at U = 8 unbounded.
+template <int WB, class IA, class IB, bool CHECK_B, int U, int MINB>
+__global__ void __launch_bounds__(kGatherThreads, MINB)
     k_join_rows(const uint8_t* __restrict__ ta, IA ia, uint32_t wa, const uint8_t* __restrict__ tb, IB ib,
                 uint32_t wb, uint64_t nrows_b, uint8_t* __restrict__ out, uint64_t n, FastDiv fd_row,
                 uint32_t pk_off, int pk_check, int* err) {
@@ -468,19 +474,19 @@ __global__ void __launch_bounds__(kGatherThreads)
   T* o = reinterpret_cast<T*>(out);
   const uint32_t row_w = wa + wb;
   const uint64_t total = n * row_w;
-  const uint64_t step = (uint64_t)gridDim.x * kGatherThreads * kGatherUnroll;
+  const uint64_t step = (uint64_t)gridDim.x * kGatherThreads * U;
   const uint32_t pk_w0 = pk_off / WB, pk_w1 = (pk_off + 8 + WB - 1) / WB;
   // word t = row r, word w of the row, walked in steps of kGatherThreads words
   const uint32_t qs = (uint32_t)fdiv(kGatherThreads, fd_row), rs = kGatherThreads - qs * row_w;
   bool bad = false;
-  for (uint64_t base = (uint64_t)blockIdx.x * kGatherThreads * kGatherUnroll + threadIdx.x; base < total;
+  for (uint64_t base = (uint64_t)blockIdx.x * kGatherThreads * U + threadIdx.x; base < total;
        base += step) {
-    T v[kGatherUnroll];
-    bool ok[kGatherUnroll];
+    T v[U];
+    bool ok[U];
     uint64_t r = fdiv(base, fd_row);
     uint32_t w = (uint32_t)(base - r * row_w);
 #pragma unroll
-    for (int k = 0; k < kGatherUnroll; ++k) {
+    for (int k = 0; k < U; ++k) {
       const uint64_t t = base + (uint64_t)k * kGatherThreads;
       ok[k] = false;
       if (t < total) {
@@ -507,26 +513,26 @@ __global__ void __launch_bounds__(kGatherThreads)
       }
     }
 #pragma unroll
-    for (int k = 0; k < kGatherUnroll; ++k)
+    for (int k = 0; k < U; ++k)
       if (ok[k]) o[base + (uint64_t)k * kGatherThreads] = v[k];
   }
   if (bad) atomicOr(err, ERR_RANGE);
 }
 
-template <class IA, class IB, bool CHECK_B>
+template <class IA, class IB, bool CHECK_B, int U, int MINB>
 void launch_join_rows(dpg_ctx& ctx, const char* name, uint32_t WB, const uint8_t* ta, IA ia, uint32_t a_bytes,
                       const uint8_t* tb, IB ib, uint32_t b_bytes, uint64_t nrows_b, uint8_t* out, uint64_t n,
                       uint32_t pk_off, int pk_check, cudaStream_t st) {
   const uint32_t wa = a_bytes / WB, wb = b_bytes / WB;
   const FastDiv f = make_fastdiv(wa + wb);
   const uint64_t total = n * (wa + wb);
-  const uint64_t per_block = (uint64_t)kGatherThreads * kGatherUnroll;
+  const uint64_t per_block = (uint64_t)kGatherThreads * U;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((total + per_block - 1) / per_block,
                                                                   (uint64_t)ctx.sms * 8));
   TraceScope ts(ctx, name, st);
 #define DPG_JOIN(WBV)                                                                                           \
-  k_join_rows<WBV, IA, IB, CHECK_B><<<grid, kGatherThreads, 0, st>>>(ta, ia, wa, tb, ib, wb, nrows_b, out, n, f, \
-                                                                     pk_off, pk_check, ctx.d_err)
+  k_join_rows<WBV, IA, IB, CHECK_B, U, MINB><<<grid, kGatherThreads, 0, st>>>(ta, ia, wa, tb, ib, wb, nrows_b, out, \
+                                                                              n, f, pk_off, pk_check, ctx.d_err)
   switch (WB) {
     case 16: DPG_JOIN(16); break;
     case 8: DPG_JOIN(8); break;
@@ -597,13 +603,13 @@ void launch_join_phase3(dpg_ctx& ctx, const Retrieval& r, const uint8_t* stage, 
                                 pow2_align(reinterpret_cast<uintptr_t>(j.fact)),
                                 pow2_align(reinterpret_cast<uintptr_t>(j.dim))});
   if (j.mode == 0)
-    launch_join_rows<RowIdentity, RowSlot, false>(ctx, "k_join_move_rows", wb, j.fact, RowIdentity{}, j.fact_bytes,
-                                                  stage, RowSlot{slot}, j.dim_bytes, j.n_dim, j.out, r.n, j.pk_off,
-                                                  0, r.stream);
+    launch_join_rows<RowIdentity, RowSlot, false, 8, 0>(ctx, "k_join_move_rows", wb, j.fact, RowIdentity{},
+                                                        j.fact_bytes, stage, RowSlot{slot}, j.dim_bytes, j.n_dim,
+                                                        j.out, r.n, j.pk_off, 0, r.stream);
   else
-    launch_join_rows<RowSlot, RowPairKey, false>(ctx, "k_join_sort_rows", wb, stage, RowSlot{slot}, j.fact_bytes,
-                                                 j.dim, RowPairKey{j.sorted_pairs, j.key_bytes}, j.dim_bytes,
-                                                 j.n_dim, j.out, r.n, j.pk_off, 1, r.stream);
+    launch_join_rows<RowSlot, RowPairKey, false, 8, 0>(ctx, "k_join_sort_rows", wb, stage, RowSlot{slot},
+                                                       j.fact_bytes, j.dim, RowPairKey{j.sorted_pairs, j.key_bytes},
+                                                       j.dim_bytes, j.n_dim, j.out, r.n, j.pk_off, 1, r.stream);
 }
 
 namespace {
@@ -889,9 +895,9 @@ int run_join_direct(dpg_ctx& ctx, const JoinSpec& j, uint64_t n_fact, cudaStream
                                 pow2_align(reinterpret_cast<uintptr_t>(j.out)),
                                 pow2_align(reinterpret_cast<uintptr_t>(j.fact)),
                                 pow2_align(reinterpret_cast<uintptr_t>(j.dim))});
-  launch_join_rows<RowIdentity, RowField, true>(ctx, "k_join_direct_rows", wb, j.fact, RowIdentity{}, j.fact_bytes,
-                                                j.dim, RowField{j.fact + j.fk_off, j.fact_bytes}, j.dim_bytes,
-                                                j.n_dim, j.out, n_fact, j.pk_off, 1, st);
+  launch_join_rows<RowIdentity, RowField, true, 4, 8>(ctx, "k_join_direct_rows", wb, j.fact, RowIdentity{},
+                                                      j.fact_bytes, j.dim, RowField{j.fact + j.fk_off, j.fact_bytes},
+                                                      j.dim_bytes, j.n_dim, j.out, n_fact, j.pk_off, 1, st);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "join direct launch");
 }

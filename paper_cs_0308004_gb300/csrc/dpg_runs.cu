@@ -367,9 +367,10 @@ struct JoinTail {
   uint32_t pk_off;
   FastDiv fd_row;  // fact-row words + wd
 };
-// join-row words in flight per thread; the join tile runs two CTAs per SM
-// (64 registers; unbounded it takes 80 and one CTA)
-constexpr int kJoinUnroll = 4;
+// join-row words in flight per thread (2: 4.77 ms on the 2e8-row join, 4:
+// 5.05 ms, 8: 5.93 ms); the join tile runs two CTAs per SM (64 registers;
+// unbounded it takes 80 and one CTA)
+constexpr int kJoinUnroll = 2;
 
 template <int WB, int IPT, bool STAGE, bool VEC, bool JOIN = false>
 __global__ void __launch_bounds__(kTileThreads, JOIN ? 2 : 1)

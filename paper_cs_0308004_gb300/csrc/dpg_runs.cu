@@ -369,11 +369,13 @@ struct JoinTail {
 };
 // join-row words in flight per thread (2: 4.77 ms on the 2e8-row join, 4:
 // 5.05 ms, 8: 5.93 ms); the join tile runs two CTAs per SM (64 registers;
-// unbounded it takes 80 and one CTA)
+// unbounded it takes 80 and one CTA).  The record tiles stay unbounded: an
+// explicit minimum of one CTA lets the compiler take up to 79 registers
+// where it otherwise takes 32-60.
 constexpr int kJoinUnroll = 2;
 
 template <int WB, int IPT, bool STAGE, bool VEC, bool JOIN = false>
-__global__ void __launch_bounds__(kTileThreads, JOIN ? 2 : 1)
+__global__ void __launch_bounds__(kTileThreads, JOIN ? 2 : 0)
     k_unpart_runs(uint64_t n, uint32_t nb, uint32_t G, uint64_t per, const uint32_t* __restrict__ off,
                   const uint32_t* __restrict__ cur_g, const uint16_t* __restrict__ tpos,
                   const uint16_t* __restrict__ tcnt_g, const uint8_t* __restrict__ internal,

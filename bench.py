@@ -92,11 +92,11 @@ def args_():
 # to `src_sha256` (any edit of them nulls the figure).
 NCU_TRAFFIC = {
     "src_sha256": "6f6c77536833accbe0314011a52a87e6d9bde62178d7e1702c0e74d2be84dbd4"
-                  ":8fd3c051dcd2bb149256617ee83296f6be783ea27ecf845a6e2b85da7af5ced2"
+                  ":b6d891f51824785d4ea16ceb6b6f6e8abc5d2bda6411333597cb7a38338e2ebf"
                   ":3855e8849060e1679f0ff4c0a4d780ef201c67030b4327071279271201401681",
     "n": 10_000_000, "rec": 100,
-    "bytes": {"4/k_probe_l2": 1040027136 + 959667456, "4/k_gather_phase3": 1061097472 + 955095552,
-              "3/k_probe": 1020253696 + 944071424, "3/k_gather_phase3": 1040537344 + 955564288},
+    "bytes": {"4/k_probe_l2": 1040257792 + 959681024, "4/k_gather_phase3": 1060956416 + 955388416,
+              "3/k_probe": 1020185856 + 943697664, "3/k_gather_phase3": 1040556032 + 955550976},
 }
 
 TRAFFIC_SOURCES = ("dpg_retrieve.cu", "dpg_runs.cu", "dpg_device.cuh")

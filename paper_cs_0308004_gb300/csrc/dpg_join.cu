@@ -21,11 +21,16 @@ namespace dpg {
 namespace {
 
 // Pair i of the DPG-sort join (8 bytes): key bytes [0, kb) = fk big-endian
-// in the first word, rid = i in the second.  A foreign key outside
-// [0, n_dim) raises the range bit.
+// in the first word, rid = i in the second; the digit counts of each key
+// byte are taken on the way (counts[j * 256 + d], zero on entry).  A
+// foreign key outside [0, n_dim) raises the range bit.
 __global__ void __launch_bounds__(256)
     k_extract_fk_pairs(const uint8_t* __restrict__ fact, uint64_t n, uint32_t fact_bytes, uint32_t fk_off,
-                       uint64_t n_dim, uint32_t kb, uint2* __restrict__ pairs, int* err) {
+                       uint64_t n_dim, uint32_t kb, uint2* __restrict__ pairs, uint32_t* __restrict__ counts,
+                       int* err) {
+  __shared__ uint32_t h[4 * 256];
+  for (uint32_t x = threadIdx.x; x < kb * 256; x += blockDim.x) h[x] = 0;
+  __syncthreads();
   bool bad = false;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t fk = (uint32_t)__ldg(reinterpret_cast<const int32_t*>(fact + i * fact_bytes + fk_off));
@@ -33,7 +38,11 @@ __global__ void __launch_bounds__(256)
     uint32_t key = 0;
     for (uint32_t j = 0; j < kb; ++j) key |= ((fk >> (8 * (kb - 1 - j))) & 0xffu) << (8 * j);
     pairs[i] = make_uint2(key, (uint32_t)i);
+    for (uint32_t j = 0; j < kb; ++j) atomicAdd(&h[j * 256 + ((key >> (8 * j)) & 0xffu)], 1u);
   }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < kb * 256; x += blockDim.x)
+    if (h[x]) atomicAdd(&counts[x], h[x]);
   if (bad) atomicOr(err, ERR_RANGE);
 }
 
@@ -98,15 +107,17 @@ extern "C" dpg_status dpg_fk_join(dpg_ctx* c, const void* fact_v, size_t n_fact,
   const size_t bp = al(n_fact * 8), bs = sort_scan_bytes(n_fact);
   if (int s = ensure_aux(*c, 2 * bp + bs)) return (dpg_status)s;
   uint8_t* a = static_cast<uint8_t*>(c->aux);
+  uint32_t* counts = radix_counts(a + 2 * bp);
+  if (cudaError_t e = cudaMemsetAsync(counts, 0, 12 * 256 * 4, st)) return (dpg_status)cuda_fail(*c, e, "memset");
   {
     TraceScope ts(*c, "k_extract_fk_pairs", st);
     const int grid = (int)std::min<uint64_t>((n_fact + 255) / 256, (uint64_t)c->sms * 8);
     k_extract_fk_pairs<<<grid, 256, 0, st>>>(fact, n_fact, (uint32_t)fact_bytes, (uint32_t)fk_off, n_dim, kb,
-                                             reinterpret_cast<uint2*>(a), c->d_err);
+                                             reinterpret_cast<uint2*>(a), counts, c->d_err);
     c->launches++;
   }
   int status = DPG_OK;
-  uint8_t* sorted = run_radix_pairs8(*c, a, a + bp, a + 2 * bp, n_fact, kb, st, &status);
+  uint8_t* sorted = run_radix_pairs8(*c, a, a + bp, a + 2 * bp, n_fact, kb, st, &status, true);
   if (status != DPG_OK) return (dpg_status)status;
   j.sorted_pairs = sorted;
   j.key_bytes = kb;

@@ -38,10 +38,15 @@ template <class E> __host__ __device__ constexpr uint32_t rs_tile() { return kRs
 // Phase 1: pairs[i] = (key of record i, zero pad, i).  WORDS: records and
 // the table are 4-byte aligned, so the key is read as ceil(key_bytes/4)
 // words (never past the record: key_bytes <= rec, rec a multiple of 4).
+// The digit counts of every key byte (counts[j * 256 + d], zero on entry)
+// are taken on the way, so the radix sort need not read the pairs for them.
 template <bool WORDS>
 __global__ void __launch_bounds__(256)
     k_extract_pairs(const uint8_t* __restrict__ src, uint64_t n, uint32_t rec, uint32_t key_bytes,
-                    uint4* __restrict__ pairs) {
+                    uint4* __restrict__ pairs, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t h[12 * 256];
+  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x) h[x] = 0;
+  __syncthreads();
   const uint32_t nw = (key_bytes + 3) / 4;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint8_t* r = src + i * rec;
@@ -61,7 +66,11 @@ __global__ void __launch_bounds__(256)
         if (b < key_bytes) w[b >> 2] |= (uint32_t)__ldg(r + b) << (8 * (b & 3));
     }
     pairs[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    for (uint32_t j = 0; j < key_bytes; ++j) atomicAdd(&h[j * 256 + ((w[j >> 2] >> (8 * (j & 3))) & 0xffu)], 1u);
   }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x)
+    if (h[x]) atomicAdd(&counts[x], h[x]);
 }
 
 // Key byte `byte` of a pair: 16-byte pairs hold up to 12 key bytes in words
@@ -247,7 +256,8 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
 
 // Phases 1 and 2 of §3: sorted key-pointer pairs of src into `pairs`
 // (n_src x 16 bytes).  `tmp` is n_src x 16 bytes of scratch; `scan` holds the
-// count matrix and scan buffers (see sort_scan_bytes).
+// digit-count matrix (12 x 256 words at its start), the tile counter and the
+// tiles' published counts (see sort_scan_bytes).
 size_t sort_scan_bytes(uint64_t n) {
   const uint64_t ntiles = (n + rs_tile<uint4>() - 1) / rs_tile<uint4>();  // the smaller tile: the most tiles
   return ((256 * ntiles * 4 + 255) & ~255ull) + 16384;
@@ -257,7 +267,7 @@ namespace {
 
 template <class E>
 uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint64_t n, uint32_t key_bytes,
-                     cudaStream_t st, int* status) {
+                     cudaStream_t st, int* status, bool counted) {
   *status = DPG_OK;
   E* a = reinterpret_cast<E*>(a_);
   E* b = reinterpret_cast<E*>(b_);
@@ -267,16 +277,16 @@ uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint
     return nullptr;
   }
   const uint32_t ntiles = (uint32_t)((n + rs_tile<E>() - 1) / rs_tile<E>());
-  uint32_t* tile_status = reinterpret_cast<uint32_t*>(scan);
-  uint8_t* rest = scan + ((256ull * ntiles * 4 + 255) & ~255ull);
-  uint32_t* counts = reinterpret_cast<uint32_t*>(rest);  // key_bytes x 256
+  uint32_t* counts = radix_counts(scan);  // key_bytes x 256
   uint32_t* tile_ctr = counts + 12 * 256;
-  cudaError_t e = cudaMemsetAsync(counts, 0, 12 * 256 * 4, st);
-  if (e != cudaSuccess) {
-    *status = cuda_fail(ctx, e, "memset");
-    return nullptr;
-  }
-  {
+  uint32_t* tile_status = reinterpret_cast<uint32_t*>(scan + 16384);
+  cudaError_t e = cudaSuccess;
+  if (!counted) {
+    e = cudaMemsetAsync(counts, 0, 12 * 256 * 4, st);
+    if (e != cudaSuccess) {
+      *status = cuda_fail(ctx, e, "memset");
+      return nullptr;
+    }
     TraceScope ts(ctx, "k_rs_global_hist", st);
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 1023) / 1024, (uint64_t)ctx.sms * 2));
     k_rs_global_hist<E><<<grid, 1024, 0, st>>>(a, n, key_bytes, counts);
@@ -306,14 +316,16 @@ uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint
 
 }  // namespace
 
+uint32_t* radix_counts(uint8_t* scan) { return reinterpret_cast<uint32_t*>(scan); }
+
 uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
-                         cudaStream_t st, int* status) {
-  return radix_pairs<uint4>(ctx, a, b, scan, n, key_bytes, st, status);
+                         cudaStream_t st, int* status, bool counted) {
+  return radix_pairs<uint4>(ctx, a, b, scan, n, key_bytes, st, status, counted);
 }
 
 uint8_t* run_radix_pairs8(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
-                          cudaStream_t st, int* status) {
-  return radix_pairs<uint2>(ctx, a, b, scan, n, key_bytes, st, status);
+                          cudaStream_t st, int* status, bool counted) {
+  return radix_pairs<uint2>(ctx, a, b, scan, n, key_bytes, st, status, counted);
 }
 
 int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, uint32_t key_bytes, uint8_t* pairs,
@@ -322,17 +334,21 @@ int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, 
   // an even number of passes ends where it started
   uint8_t* start = (key_bytes % 2 == 0) ? pairs : tmp;
   uint8_t* other = (key_bytes % 2 == 0) ? tmp : pairs;
+  if (key_bytes == 0 || key_bytes > 12) return DPG_EINVAL;
+  uint32_t* counts = radix_counts(scan);
+  cudaError_t e = cudaMemsetAsync(counts, 0, 12 * 256 * 4, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   {
     TraceScope ts(ctx, "k_extract_pairs", st);
     const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx.sms * 8);
     if (rec % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 4 == 0)
-      k_extract_pairs<true><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, reinterpret_cast<uint4*>(start));
+      k_extract_pairs<true><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, reinterpret_cast<uint4*>(start), counts);
     else
-      k_extract_pairs<false><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, reinterpret_cast<uint4*>(start));
+      k_extract_pairs<false><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, reinterpret_cast<uint4*>(start), counts);
     ctx.launches++;
   }
   int status = DPG_OK;
-  run_radix_pairs(ctx, start, other, scan, n, key_bytes, st, &status);
+  run_radix_pairs(ctx, start, other, scan, n, key_bytes, st, &status, true);
   return status;
 }
 

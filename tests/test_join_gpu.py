@@ -89,6 +89,25 @@ def test_join_sort_phase3_paths(ctx, monkeypatch, slot):
         assert np.array_equal(out.cpu().numpy(), want), (fb, fo, db, po)
 
 
+@pytest.mark.parametrize("variant", ["3", "4"])
+def test_join_sort_four_key_bytes(ctx, monkeypatch, variant):
+    """More than 2**24 dimension rows: the DPG-sort join sorts its 8-byte
+    pairs on all four bytes of the foreign key (keys whose top byte is set,
+    repeated keys, a ragged last tile); rows against the oracle."""
+    monkeypatch.setenv("DPG_VARIANT", variant)
+    n_dim, n_fact = (1 << 24) + 5, 200_003
+    d = np.arange(n_dim, dtype="<i8").view(np.uint8).reshape(n_dim, 8)     # 8-byte rows: the key alone
+    fk = synth.uniform_ids(n_fact, n_dim, 31).astype(np.int64)
+    fk[:4] = [n_dim - 1, 0, 1 << 24, (1 << 24) + 2]
+    fk[100:140] = fk[7]                                                     # a run of equal keys
+    f = synth.records(n_fact, 16, 32).copy()
+    f[:, :4] = fk.astype("<i4").view(np.uint8).reshape(n_fact, 4)
+    want = oracle.fk_join_sorted(f, d)
+    out = ctx.fk_join(to_dev(f), to_dev(d), "sort")
+    ctx.sync()
+    assert np.array_equal(out.cpu().numpy(), want)
+
+
 @pytest.mark.parametrize("mode", ["move", "sort"])
 @pytest.mark.parametrize("variant", ["3", "4"])
 def test_join_bad_keys_each_plan(ctx, monkeypatch, variant, mode):

@@ -7,9 +7,10 @@
 // strings; equal keys keep rid order.
 //
 // Phase 2 is a stable least-significant-digit radix sort with one key byte
-// per pass (byte key_bytes-1 first, byte 0 last).  k_rs_global_hist counts
-// every key byte's digits over all pairs once (the counts do not depend on
-// the order).  Each pass is then one kernel, k_rs_onesweep: a CTA takes the
+// per pass (byte key_bytes-1 first, byte 0 last).  Every key byte's digits
+// are counted over all pairs once (the counts do not depend on the order):
+// by the kernel that builds the pairs (k_extract_pairs here, the join's
+// k_extract_fk_pairs), or by k_rs_global_hist for pairs built elsewhere.  Each pass is then one kernel, k_rs_onesweep: a CTA takes the
 // next tile (64 KB of pairs), ranks them stably (per-warp digit counts, the
 // lanes sharing a digit found with a shared-memory OR, prefix over warps),
 // publishes its digit counts, and

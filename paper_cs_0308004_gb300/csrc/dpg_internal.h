@@ -158,14 +158,13 @@ int run_join_direct(dpg_ctx& ctx, const JoinSpec& j, uint64_t n_fact, cudaStream
 // `a` holds the pairs; the result ends in `a` (even key_bytes) or `b`; the
 // returned pointer says which.  run_radix_pairs8: the same for 8-byte pairs
 // (key bytes [0, key_bytes <= 4) in the first word, the rid in the second).
-// counted: the caller has already filled radix_counts(scan) (digit counts
-// of key byte j at [j * 256, j * 256 + 256), zeroed first) while building
-// the pairs, so they are not counted again.
+// The caller fills radix_counts(scan) while it builds the pairs: the count
+// of digit d of key byte j over all pairs at [j * 256 + d] (zeroed first).
 uint32_t* radix_counts(uint8_t* scan);
 uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
-                         cudaStream_t st, int* status, bool counted = false);
+                         cudaStream_t st, int* status);
 uint8_t* run_radix_pairs8(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
-                          cudaStream_t st, int* status, bool counted = false);
+                          cudaStream_t st, int* status);
 
 // Phases 1-2 of the §3 sort (dpg_sort.cu): sorted 16-byte key-pointer pairs.
 size_t sort_scan_bytes(uint64_t n);

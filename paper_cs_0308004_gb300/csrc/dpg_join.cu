@@ -117,7 +117,7 @@ extern "C" dpg_status dpg_fk_join(dpg_ctx* c, const void* fact_v, size_t n_fact,
     c->launches++;
   }
   int status = DPG_OK;
-  uint8_t* sorted = run_radix_pairs8(*c, a, a + bp, a + 2 * bp, n_fact, kb, st, &status, true);
+  uint8_t* sorted = run_radix_pairs8(*c, a, a + bp, a + 2 * bp, n_fact, kb, st, &status);
   if (status != DPG_OK) return (dpg_status)status;
   j.sorted_pairs = sorted;
   j.key_bytes = kb;

@@ -8,9 +8,9 @@
 //
 // Phase 2 is a stable least-significant-digit radix sort with one key byte
 // per pass (byte key_bytes-1 first, byte 0 last).  Every key byte's digits
-// are counted over all pairs once (the counts do not depend on the order):
-// by the kernel that builds the pairs (k_extract_pairs here, the join's
-// k_extract_fk_pairs), or by k_rs_global_hist for pairs built elsewhere.  Each pass is then one kernel, k_rs_onesweep: a CTA takes the
+// are counted over all pairs once, by the kernel that builds the pairs
+// (k_extract_pairs here, the join's k_extract_fk_pairs): the counts do not
+// depend on the order.  Each pass is then one kernel, k_rs_onesweep: a CTA takes the
 // next tile (64 KB of pairs), ranks them stably (per-warp digit counts, the
 // lanes sharing a digit found with a shared-memory OR, prefix over warps),
 // publishes its digit counts, and
@@ -82,22 +82,6 @@ __device__ __forceinline__ uint32_t pair_digit(const uint4& p, uint32_t byte) {
 }
 __device__ __forceinline__ uint32_t pair_digit(const uint2& p, uint32_t byte) {
   return (p.x >> (8 * (byte & 3))) & 0xffu;
-}
-
-// Digit counts of every key byte over all pairs: counts[j * 256 + d].
-template <class E>
-__global__ void __launch_bounds__(1024)
-    k_rs_global_hist(const E* __restrict__ in, uint64_t n, uint32_t key_bytes, uint32_t* __restrict__ counts) {
-  __shared__ uint32_t h[12 * 256];
-  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x) h[x] = 0;
-  __syncthreads();
-  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x) {
-    const E v = in[e];
-    for (uint32_t j = 0; j < key_bytes; ++j) atomicAdd(&h[j * 256 + pair_digit(v, j)], 1u);
-  }
-  __syncthreads();
-  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x)
-    if (h[x]) atomicAdd(&counts[x], h[x]);
 }
 
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kCountMask = (1u << 30) - 1;
@@ -268,7 +252,7 @@ namespace {
 
 template <class E>
 uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint64_t n, uint32_t key_bytes,
-                     cudaStream_t st, int* status, bool counted) {
+                     cudaStream_t st, int* status) {
   *status = DPG_OK;
   E* a = reinterpret_cast<E*>(a_);
   E* b = reinterpret_cast<E*>(b_);
@@ -278,21 +262,10 @@ uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint
     return nullptr;
   }
   const uint32_t ntiles = (uint32_t)((n + rs_tile<E>() - 1) / rs_tile<E>());
-  uint32_t* counts = radix_counts(scan);  // key_bytes x 256
-  uint32_t* tile_ctr = counts + 12 * 256;
+  const uint32_t* counts = radix_counts(scan);  // key_bytes x 256, filled by the caller
+  uint32_t* tile_ctr = radix_counts(scan) + 12 * 256;
   uint32_t* tile_status = reinterpret_cast<uint32_t*>(scan + 16384);
   cudaError_t e = cudaSuccess;
-  if (!counted) {
-    e = cudaMemsetAsync(counts, 0, 12 * 256 * 4, st);
-    if (e != cudaSuccess) {
-      *status = cuda_fail(ctx, e, "memset");
-      return nullptr;
-    }
-    TraceScope ts(ctx, "k_rs_global_hist", st);
-    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 1023) / 1024, (uint64_t)ctx.sms * 2));
-    k_rs_global_hist<E><<<grid, 1024, 0, st>>>(a, n, key_bytes, counts);
-    ctx.launches++;
-  }
   const size_t smem = rs_tile<E>() * (sizeof(E) + 1);
   cudaFuncSetAttribute(k_rs_onesweep<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (int byte = (int)key_bytes - 1; byte >= 0; --byte) {
@@ -320,13 +293,13 @@ uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint
 uint32_t* radix_counts(uint8_t* scan) { return reinterpret_cast<uint32_t*>(scan); }
 
 uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
-                         cudaStream_t st, int* status, bool counted) {
-  return radix_pairs<uint4>(ctx, a, b, scan, n, key_bytes, st, status, counted);
+                         cudaStream_t st, int* status) {
+  return radix_pairs<uint4>(ctx, a, b, scan, n, key_bytes, st, status);
 }
 
 uint8_t* run_radix_pairs8(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
-                          cudaStream_t st, int* status, bool counted) {
-  return radix_pairs<uint2>(ctx, a, b, scan, n, key_bytes, st, status, counted);
+                          cudaStream_t st, int* status) {
+  return radix_pairs<uint2>(ctx, a, b, scan, n, key_bytes, st, status);
 }
 
 int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, uint32_t key_bytes, uint8_t* pairs,
@@ -349,7 +322,7 @@ int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, 
     ctx.launches++;
   }
   int status = DPG_OK;
-  run_radix_pairs(ctx, start, other, scan, n, key_bytes, st, &status, true);
+  run_radix_pairs(ctx, start, other, scan, n, key_bytes, st, &status);
   return status;
 }
 

@@ -92,7 +92,7 @@ def args_():
 # to `src_sha256` (any edit of them nulls the figure).
 NCU_TRAFFIC = {
     "src_sha256": "6f6c77536833accbe0314011a52a87e6d9bde62178d7e1702c0e74d2be84dbd4"
-                  ":b6d891f51824785d4ea16ceb6b6f6e8abc5d2bda6411333597cb7a38338e2ebf"
+                  ":ea4aa05df714562de946e6caba3cc9da73b7638cf8349e76339692c3d9d2f8e6"
                   ":3855e8849060e1679f0ff4c0a4d780ef201c67030b4327071279271201401681",
     "n": 10_000_000, "rec": 100,
     "bytes": {"4/k_probe_l2": 1040257792 + 959681024, "4/k_gather_phase3": 1060956416 + 955388416,

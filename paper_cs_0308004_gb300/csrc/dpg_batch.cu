@@ -223,7 +223,8 @@ extern "C" dpg_status dpg_retrieve_batch(dpg_ctx* c, const dpg_request* reqs, si
     if (int s = run_dpg(*c, r, choose_plan(*c, r))) return (dpg_status)s;
     if (!g.dst_in_place) {
       uint32_t wb = align_of(rec);
-      for (size_t i = g.first; i < g.last; ++i) wb = std::min(wb, align_of(reinterpret_cast<uintptr_t>(reqs[live[i]].dst)));
+      for (size_t i = g.first; i < g.last; ++i)
+        wb = std::min(wb, align_of(reinterpret_cast<uintptr_t>(reqs[live[i]].dst)));
       const uint32_t W = rec / wb;
       const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((g.total + kBatchChunk - 1) / kBatchChunk,
                                                                     (uint64_t)c->sms * 4));

@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     {
       const uint32_t m = (uint32_t)((hi - lo) < (uint64_t)T ? (hi - lo) : (uint64_t)T);
 #pragma unroll
-      for (int k = 0; k < IPT; ++k) r[k] = k * kTileThreads + tid < m ? (uint32_t)__ldg(rid + lo + k * kTileThreads + tid) : 0u;
+      for (int k = 0; k < IPT; ++k)
+        r[k] = k * kTileThreads + tid < m ? (uint32_t)__ldg(rid + lo + k * kTileThreads + tid) : 0u;
     }
     for (uint64_t t0 = lo; t0 < hi; t0 += T) {
       const uint32_t tn = (uint32_t)((hi - t0) < (uint64_t)T ? (hi - t0) : (uint64_t)T);
@@ -229,7 +230,8 @@ __global__ void __launch_bounds__(kTileThreads, 3)
           for (int k = 0; k < IPT; ++k) rn[k] = (uint32_t)__ldg(rt + k * kTileThreads + tid);
         } else {
 #pragma unroll
-          for (int k = 0; k < IPT; ++k) rn[k] = k * kTileThreads + tid < m ? (uint32_t)__ldg(rt + k * kTileThreads + tid) : 0u;
+          for (int k = 0; k < IPT; ++k)
+            rn[k] = k * kTileThreads + tid < m ? (uint32_t)__ldg(rt + k * kTileThreads + tid) : 0u;
         }
       }
       // count, and each rid's rank among the tile's rids of its run
@@ -758,7 +760,8 @@ int run_dpg_l2_t(dpg_ctx& ctx, const Retrieval& r, Rid rid, const Plan& plan) {
   if (r.join && !L.slot_mode) {
     TraceScope ts(ctx, "k_unpart_join", r.stream);
     const JoinSpec& j = *r.join;
-    const uint32_t wb3 = std::min({pow2_align(r.rec), pow2_align(j.dim_bytes), pow2_align(reinterpret_cast<uintptr_t>(j.out)),
+    const uint32_t wb3 = std::min({pow2_align(r.rec), pow2_align(j.dim_bytes),
+                                   pow2_align(reinterpret_cast<uintptr_t>(j.out)),
                                    pow2_align(reinterpret_cast<uintptr_t>(j.dim))});
     switch (wb3) {
       case 16: launch_unpart_join<16>(ctx, L, r, off, cnt, tpos, tcnt, stage); break;

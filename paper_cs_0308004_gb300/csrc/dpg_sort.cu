@@ -34,7 +34,8 @@ constexpr int kRsThreads = 512;
 constexpr int kRsMinBlocks = 2;
 constexpr int kRsWarps = kRsThreads / 32;
 template <class E> __host__ __device__ constexpr int rs_items() { return sizeof(E) == 16 ? 8 : 16; }
-template <class E> __host__ __device__ constexpr uint32_t rs_tile() { return kRsThreads * rs_items<E>(); }  // pairs per tile
+// pairs per tile
+template <class E> __host__ __device__ constexpr uint32_t rs_tile() { return kRsThreads * rs_items<E>(); }
 
 // Phase 1: pairs[i] = (key of record i, zero pad, i).  WORDS: records and
 // the table are 4-byte aligned, so the key is read as ceil(key_bytes/4)

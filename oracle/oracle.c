@@ -19,6 +19,7 @@
  * sortedness + permutation + tie order for the key-pointer sort (§3);
  * nested-loop agreement for the foreign-key joins (§4.2).
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -37,6 +38,68 @@ int oracle_retrieve(const uint8_t* src, uint64_t n_src, uint64_t rec, uint64_t n
   for (uint64_t i = 0; i < n; ++i)
     memcpy(dst + i * rec, src + (uint64_t)rids[i] * rec, rec);
   return OR_OK;
+}
+
+/* The same retrieval on `threads` POSIX threads, for the benchmark's
+ * multi-core CPU figure: the threads first check the rids of their own
+ * contiguous ranges of destination slots and, only if every rid of every range
+ * is in [0, n_src), then copy those ranges.  The tests check it against
+ * oracle_retrieve. */
+struct or_range {
+  const uint8_t* src;
+  uint64_t n_src, rec, lo, hi;
+  const int32_t* rids;
+  uint8_t* dst;
+  int bad;
+};
+
+static void* or_check_range(void* arg) {
+  struct or_range* r = (struct or_range*)arg;
+  for (uint64_t i = r->lo; i < r->hi; ++i)
+    if (r->rids[i] < 0 || (uint64_t)r->rids[i] >= r->n_src) r->bad = 1;
+  return NULL;
+}
+
+static void* or_copy_range(void* arg) {
+  struct or_range* r = (struct or_range*)arg;
+  for (uint64_t i = r->lo; i < r->hi; ++i)
+    memcpy(r->dst + i * r->rec, r->src + (uint64_t)r->rids[i] * r->rec, r->rec);
+  return NULL;
+}
+
+static int or_run_ranges(struct or_range* ranges, pthread_t* tids, uint64_t threads, void* (*fn)(void*)) {
+  uint64_t started = 0;
+  int rc = OR_OK;
+  for (; started < threads; ++started)
+    if (pthread_create(&tids[started], NULL, fn, &ranges[started]) != 0) {
+      rc = OR_ENOMEM;
+      break;
+    }
+  for (uint64_t t = 0; t < started; ++t) pthread_join(tids[t], NULL);
+  return rc;
+}
+
+int oracle_retrieve_threads(const uint8_t* src, uint64_t n_src, uint64_t rec, uint64_t n,
+                            const int32_t* rids, uint8_t* dst, uint64_t threads) {
+  if (rec == 0 || threads == 0) return OR_EINVAL;
+  if (threads > n) threads = n ? n : 1;
+  struct or_range* ranges = calloc(threads, sizeof *ranges);
+  pthread_t* tids = calloc(threads, sizeof *tids);
+  if (!ranges || !tids) {
+    free(ranges);
+    free(tids);
+    return OR_ENOMEM;
+  }
+  for (uint64_t t = 0; t < threads; ++t) {
+    ranges[t] = (struct or_range){src, n_src, rec, n * t / threads, n * (t + 1) / threads, rids, dst, 0};
+  }
+  int rc = or_run_ranges(ranges, tids, threads, or_check_range);
+  for (uint64_t t = 0; rc == OR_OK && t < threads; ++t)
+    if (ranges[t].bad) rc = OR_ERANGE;
+  if (rc == OR_OK) rc = or_run_ranges(ranges, tids, threads, or_copy_range);
+  free(ranges);
+  free(tids);
+  return rc;
 }
 
 /* §2.1 three phases and Figure 1, for small inputs, with runs numbered from 0

@@ -109,6 +109,24 @@ def test_retrieve_out_of_range_writes_nothing(bad):
     assert np.all(dst == 0x5A)
 
 
+@pytest.mark.parametrize("threads", [1, 3, 16, 200])
+def test_retrieve_threads_equals_retrieve(threads):
+    """The multi-core retrieval (the benchmark's CPU figure) gives the plain
+    retrieval's bytes, with more threads than records too, and on a bad rid
+    reports it and writes nothing."""
+    for n, rec in ((0, 8), (1, 3), (150, 100), (1009, 17)):
+        src = synth.records(64, rec, 5)
+        rids = synth.uniform_ids(n, 64, 6)
+        assert np.array_equal(oracle.retrieve_threads(src, rids, threads), oracle.retrieve(src, rids))
+    src = synth.records(64, 12, 7)
+    rids = synth.uniform_ids(500, 64, 8)
+    rids[377] = 64
+    out = np.full((500, 12), 0x5A, np.uint8)
+    with pytest.raises(oracle.OracleRangeError):
+        oracle.retrieve_threads(src, rids, threads, out=out)
+    assert bool((out == 0x5A).all())
+
+
 def test_retrieve_empty():
     src = synth.records(10, 8, 1)
     assert oracle.retrieve(src, np.zeros(0, np.int32)).shape == (0, 8)

@@ -10,14 +10,14 @@
 // per pass (byte key_bytes-1 first, byte 0 last).  Every key byte's digits
 // are counted over all pairs once, by the kernel that builds the pairs
 // (k_extract_pairs here, the join's k_extract_fk_pairs): the counts do not
-// depend on the order.  Each pass is then one kernel, k_rs_onesweep: a CTA takes the
-// next tile (64 KB of pairs), ranks them stably (per-warp digit counts, the
-// lanes sharing a digit found with a shared-memory OR, prefix over warps),
-// publishes its digit counts, and
-// finds how many pairs of each digit earlier tiles hold by looking back over
-// their published counts (decoupled look-back; every wait is bounded), then
-// reorders the tile in shared memory and writes each digit's pairs as one
-// contiguous piece at digit base + earlier tiles' count.
+// depend on the order.  Each pass is then one kernel, k_rs_onesweep: a CTA
+// takes the next tile (64 KB of pairs), ranks its pairs stably (per-warp
+// digit counts, the lanes sharing a digit found with a shared-memory OR, a
+// prefix over warps), publishes the tile's digit counts, finds how many pairs
+// of each digit earlier tiles hold by looking back over their published
+// counts (decoupled look-back; every wait is bounded), then reorders the tile
+// in shared memory and writes each digit's pairs as one contiguous piece at
+// digit base + earlier tiles' count.
 #include <algorithm>
 
 #include "dpg_device.cuh"

@@ -55,7 +55,8 @@ def args_():
     p.add_argument("--no-small", action="store_true",
                    help="skip the 16-byte-record point (62,500,000 records, permutation rids) of the line")
     p.add_argument("--sweep-recs", default="16,32,64,100,256", help="record sizes of --sweep")
-    p.add_argument("--sweep-impls", default="dpg_smem,dpg_l2,dpg_tuned,direct", help="implementations of --sweep")
+    p.add_argument("--sweep-impls", default="dpg_smem,dpg_2pass,dpg_l2,dpg_tuned,direct",
+                   help="implementations of --sweep")
     p.add_argument("--sweep-bytes", type=float, default=1e9, help="source bytes per record size of --sweep")
     p.add_argument("--join", action="store_true",
                    help="foreign-key join workload (10,000,000 x 64-byte dimension, 200,000,000 x 16-byte fact, "
@@ -292,8 +293,9 @@ def run_sweep(a):
         out = torch.empty((n, rec), dtype=torch.uint8, device=dev)
         res, kern = {}, {}
         tuned = ctx.tune(d_src, d_rids, out) if "dpg_tuned" in a.sweep_impls.split(",") else None
-        for name, variant, fn in (("dpg_smem", "3", ctx.retrieve), ("dpg_l2", "4", ctx.retrieve),
-                                  ("dpg_tuned", "", ctx.retrieve), ("direct", None, ctx.retrieve_direct)):
+        for name, variant, fn in (("dpg_smem", "3", ctx.retrieve), ("dpg_2pass", "2", ctx.retrieve),
+                                  ("dpg_l2", "4", ctx.retrieve), ("dpg_tuned", "", ctx.retrieve),
+                                  ("direct", None, ctx.retrieve_direct)):
             if name not in a.sweep_impls.split(","):
                 continue
             if variant:
@@ -329,7 +331,7 @@ def run_sweep(a):
             line[f"{name}_ms"] = round(ms, 4)
         if tuned:
             line["tuned_plan"] = {"variant": tuned[0], "seg_log2": tuned[1]}
-        for name in ("dpg_smem", "dpg_l2", "dpg_tuned"):
+        for name in ("dpg_smem", "dpg_2pass", "dpg_l2", "dpg_tuned"):
             if name in res and "direct" in res:
                 line[f"{name}_speedup_vs_direct"] = round(res["direct"] / res[name], 4)
         line["kernels_us"] = kern

@@ -239,6 +239,34 @@ dpg_status dpg_sync(dpg_ctx* ctx, void* stream);
 uint64_t dpg_kernel_launches(dpg_ctx* ctx);
 
 /*
+ * Failure detection (the paper has none; these bound and exercise the
+ * library's own device-side waits).
+ *
+ * dpg_set_wait_limit: every wait of this context's kernels on a flag that
+ * another CTA writes (the radix sort's look-back over earlier tiles, the
+ * batch executor's waits for a request's earlier phase) gives up after
+ * `seconds` of SM clock (default about 1 s), sets the timeout bit and lets
+ * the kernel return; the next dpg_sync reports DPG_ETIMEOUT.  Results of a
+ * call whose wait ran out are undefined, but every write stays inside the
+ * call's own buffers and the context stays usable.  0 < seconds <= 60, else
+ * DPG_EINVAL.
+ *
+ * dpg_check_wait: enqueues one kernel that waits, under the context's limit,
+ * on a device word that nothing ever sets; the following dpg_sync returns
+ * DPG_ETIMEOUT once the limit has passed.  It runs the same bounded wait the
+ * sort and the batch executor use, so a caller (or a test) can see a wait
+ * run out without faulting or hanging the GPU.
+ *
+ * dpg_inject_alloc_failure: the next `count` device allocations of this
+ * context (scratch, work space, host-call buffers) fail as if cudaMalloc had
+ * failed: the call that needed one returns DPG_ENOMEM having enqueued
+ * nothing and left its destination untouched.  count 0 clears it.
+ */
+dpg_status dpg_set_wait_limit(dpg_ctx* ctx, double seconds);
+dpg_status dpg_check_wait(dpg_ctx* ctx, void* stream);
+dpg_status dpg_inject_alloc_failure(dpg_ctx* ctx, int count);
+
+/*
  * Host-buffer variants (the paper states retrieval between files, §1; here
  * the "files" are host memory).  src/pairs, rids and dst are HOST pointers
  * (page-locked memory gives full copy bandwidth).  The call copies the inputs
@@ -299,8 +327,13 @@ dpg_status dpg_trace_get(dpg_ctx* ctx, size_t index, const char** name, double* 
  *   - Limits: n <= 2,097,152 rids, rec_bytes <= 65536, and at most 4096
  *     source segments of up to 104 KB each (about 420 MB of 100-byte records);
  *     beyond them it returns DPG_EINVAL and enqueues nothing.
- *   - The first call on each device looks up the array's device address;
- *     make that first call before any stream capture.
+ *   - The first call on each device does the set-up: it looks up the
+ *     array's device address, and if no other call of this library has run
+ *     on that device yet, the CUDA runtime loads the library's device code
+ *     there (modules load lazily), which is when the array is reserved.  So
+ *     make the first call at start-up, before a caching allocator or a
+ *     memory cap takes the free memory, and before any stream capture.
+ *     Later calls allocate nothing.
  *   - The call is synchronous: it waits for `stream` and returns the final
  *     status (DPG_ERANGE for a bad rid, destination untouched).
  *   - Every call uses the same array (each call clears what must start at

@@ -53,6 +53,7 @@ _KINDS = {
     "oracle_fk_join_nested": "puuupuuupup",
     "oracle_fk_join_move": "puuupuuup",
     "oracle_fk_join_sorted": "puuupuuup",
+    "oracle_fk_join_order": "puuuup",
 }
 
 
@@ -209,3 +210,11 @@ def fk_join_sorted(fact: np.ndarray, dim: np.ndarray, fk_off: int = 0, pk_off: i
     _check(_load().oracle_fk_join_sorted(_p(fact), nf, fb, fk_off, _p(dim), nd, db, pk_off, _p(out)),
            "fk_join_sorted")
     return out
+
+
+def fk_join_order(fact: np.ndarray, n_dim: int, fk_off: int = 0) -> np.ndarray:
+    """Fact row indices in DPG-sort join order (fk, then row; §4.2.1), int64."""
+    fact, nf, fb = _records(fact)
+    order = np.empty(nf, dtype=np.uint64)
+    _check(_load().oracle_fk_join_order(_p(fact), nf, fb, fk_off, n_dim, _p(order)), "fk_join_order")
+    return order.view(np.int64)

@@ -15,7 +15,7 @@
  * rid sequences against an inverse-permutation formulation; decoding of
  * self-describing records (each record carries its own index) for duplicates,
  * exactly-once and multiset invariants; the worked example of §2.2; agreement
- * of the three-phase statement (Figure 1) with the one-line definition (§2);
+ * of the three-phase statement (§2.1) with the one-line definition (§2);
  * sortedness + permutation + tie order for the key-pointer sort (§3);
  * nested-loop agreement for the foreign-key joins (§4.2).
  */
@@ -102,17 +102,19 @@ int oracle_retrieve_threads(const uint8_t* src, uint64_t n_src, uint64_t rec, ui
   return rc;
 }
 
-/* §2.1 three phases and Figure 1, for small inputs, with runs numbered from 0
- * and run j holding rids [j*L, (j+1)*L)  (the text's "0 to L, L to 2L").
- *   Phase I  (Distribute): append each rid, in RID order, to RID_RUN[r / L].
- *   Phase II (Probe): for each run j, take each rid r of RID_RUN[j] in order and
- *            append INPUT[r] to INTERNAL run j.
- *   Phase III (Gather): for each rid r, in RID order, copy the next unread
- *            record of INTERNAL run r / L to OUTPUT.
- * Outputs: rid_runs (n rids, runs concatenated in run order), run_sizes
- * (num_runs = ceil(n_src / L) counts), internal (n records, runs concatenated),
- * dst (n records).  Run sizes follow the data: with duplicated or skewed rids a
- * run holds as many entries as rids fall in it (§2 and §2.3). */
+/* §2.1, stated as the three results its phases produce (small inputs only:
+ * the cost is quadratic).  Runs are numbered from 0 and run j covers source
+ * records [j*L, (j+1)*L).
+ *   Phase I result, the RID runs: run j is the subsequence of the rid list
+ *            formed by the rids r with r div L = j, in list order.
+ *   Phase II result, INTERNAL: entry k of the runs laid end to end (run 0
+ *            first) is the source record that rid entry k names.
+ *   Phase III result, OUTPUT: the record of rid i is the INTERNAL entry at
+ *            the start of its run j = rids[i] div L plus the number of rids
+ *            before i in the list that also fall in run j.
+ * Outputs: rid_runs (n rids, runs end to end), run_sizes (ceil(n_src / L)
+ * counts), internal (n records), dst (n records).  A run holds as many
+ * entries as rids fall in it, duplicates and skew included (§2, §2.3). */
 int oracle_dpg_phases(const uint8_t* src, uint64_t n_src, uint64_t rec, uint64_t n,
                       const int32_t* rids, uint64_t L, int32_t* rid_runs, uint64_t* run_sizes,
                       uint8_t* internal, uint8_t* dst) {
@@ -120,48 +122,28 @@ int oracle_dpg_phases(const uint8_t* src, uint64_t n_src, uint64_t rec, uint64_t
   for (uint64_t i = 0; i < n; ++i)
     if (rids[i] < 0 || (uint64_t)rids[i] >= n_src) return OR_ERANGE;
   uint64_t num_runs = (n_src + L - 1) / L;
-  /* Each run is an array with room for every rid (the plain "append"). */
-  int32_t** run = (int32_t**)calloc(num_runs ? num_runs : 1, sizeof(int32_t*));
-  uint64_t* len = (uint64_t*)calloc(num_runs ? num_runs : 1, sizeof(uint64_t));
-  uint8_t** internal_run = (uint8_t**)calloc(num_runs ? num_runs : 1, sizeof(uint8_t*));
-  uint64_t* next = (uint64_t*)calloc(num_runs ? num_runs : 1, sizeof(uint64_t));
-  int rc = OR_OK;
-  if (!run || !len || !internal_run || !next) { rc = OR_ENOMEM; goto out; }
+  /* RID runs: for each run, select its rids from the whole list, in order. */
+  uint64_t pos = 0;
   for (uint64_t j = 0; j < num_runs; ++j) {
-    run[j] = (int32_t*)malloc((n ? n : 1) * sizeof(int32_t));
-    internal_run[j] = (uint8_t*)malloc((n ? n : 1) * rec);
-    if (!run[j] || !internal_run[j]) { rc = OR_ENOMEM; goto out; }
-  }
-  /* Phase I: Distribute. */
-  for (uint64_t i = 0; i < n; ++i) {
-    uint64_t j = (uint64_t)rids[i] / L;
-    run[j][len[j]++] = rids[i];
-  }
-  /* Phase II: Probe — run j of INPUT is records [j*L, (j+1)*L). */
-  for (uint64_t j = 0; j < num_runs; ++j)
-    for (uint64_t k = 0; k < len[j]; ++k)
-      memcpy(internal_run[j] + k * rec, src + (uint64_t)run[j][k] * rec, rec);
-  /* Phase III: Gather. */
-  for (uint64_t i = 0; i < n; ++i) {
-    uint64_t j = (uint64_t)rids[i] / L;
-    memcpy(dst + i * rec, internal_run[j] + next[j] * rec, rec);
-    next[j]++;
-  }
-  {
-    uint64_t pos = 0;
-    for (uint64_t j = 0; j < num_runs; ++j) {
-      run_sizes[j] = len[j];
-      for (uint64_t k = 0; k < len[j]; ++k, ++pos) {
-        rid_runs[pos] = run[j][k];
-        memcpy(internal + pos * rec, internal_run[j] + k * rec, rec);
+    run_sizes[j] = 0;
+    for (uint64_t i = 0; i < n; ++i)
+      if ((uint64_t)rids[i] / L == j) {
+        rid_runs[pos++] = rids[i];
+        run_sizes[j]++;
       }
-    }
   }
-out:
-  if (run) for (uint64_t j = 0; j < num_runs; ++j) free(run[j]);
-  if (internal_run) for (uint64_t j = 0; j < num_runs; ++j) free(internal_run[j]);
-  free(run); free(len); free(internal_run); free(next);
-  return rc;
+  /* INTERNAL: the record each run entry names. */
+  for (uint64_t k = 0; k < n; ++k)
+    memcpy(internal + k * rec, src + (uint64_t)rid_runs[k] * rec, rec);
+  /* OUTPUT: rid i's entry = start of its run + its rank among that run's rids. */
+  for (uint64_t i = 0; i < n; ++i) {
+    uint64_t j = (uint64_t)rids[i] / L, start = 0, rank = 0;
+    for (uint64_t m = 0; m < j; ++m) start += run_sizes[m];
+    for (uint64_t m = 0; m < i; ++m)
+      if ((uint64_t)rids[m] / L == j) rank++;
+    memcpy(dst + i * rec, internal + (start + rank) * rec, rec);
+  }
+  return OR_OK;
 }
 
 /* ---- §3: three-phase sort (extract key-pointer pairs, sort them, copy). ---- */
@@ -300,5 +282,27 @@ int oracle_fk_join_sorted(const uint8_t* fact, uint64_t n_fact, uint64_t fact_by
     memcpy(out + k * w + fact_bytes, dim + (uint64_t)p[k].fk * dim_bytes, dim_bytes);
   }
   free(p);
+  return OR_OK;
+}
+
+/* The fact-row order of the DPG-sort join (§4.2.1): the row indices of the
+ * fact relation ordered by foreign key, equal keys by row index, found by a
+ * stable counting sort over the key range [0, n_dim) (every key is checked
+ * first).  order receives n_fact indices.  Linear time, so it serves the
+ * full-size join: out row j of the sorted join is the DPG-move row of fact
+ * row order[j].  The tests pin it to oracle_fk_join_sorted. */
+int oracle_fk_join_order(const uint8_t* fact, uint64_t n_fact, uint64_t fact_bytes, uint64_t fk_off,
+                         uint64_t n_dim, uint64_t* order) {
+  if (fk_off + 4 > fact_bytes) return OR_EINVAL;
+  for (uint64_t i = 0; i < n_fact; ++i) {
+    int32_t fk = rd_i32(fact + i * fact_bytes + fk_off);
+    if (fk < 0 || (uint64_t)fk >= n_dim) return OR_ERANGE;
+  }
+  uint64_t* start = (uint64_t*)calloc(n_dim + 1, sizeof(uint64_t));
+  if (!start) return OR_ENOMEM;
+  for (uint64_t i = 0; i < n_fact; ++i) start[(uint64_t)rd_i32(fact + i * fact_bytes + fk_off) + 1]++;
+  for (uint64_t k = 0; k < n_dim; ++k) start[k + 1] += start[k];  /* start[k] = rows with a smaller key */
+  for (uint64_t i = 0; i < n_fact; ++i) order[start[(uint64_t)rd_i32(fact + i * fact_bytes + fk_off)]++] = i;
+  free(start);
   return OR_OK;
 }

@@ -1,6 +1,7 @@
 // C ABI of the record-retrieval library (declarations and contracts in
 // include/dpg.h): contexts, scratch memory, argument checks and the entry
 // points that enqueue the kernels of dpg_retrieve.cu.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -94,12 +95,21 @@ static void trace_collect(dpg_ctx& ctx) {
   ctx.trace_pending.clear();
 }
 
+// An allocation the test hook dpg_inject_alloc_failure asked to fail.
+static bool injected_failure(dpg_ctx& ctx) {
+  if (ctx.fail_allocs <= 0) return false;
+  ctx.fail_allocs--;
+  ctx.last_error = "injected allocation failure";
+  return true;
+}
+
 int ensure_scratch(dpg_ctx& ctx, size_t bytes) {
   if (bytes <= ctx.scratch_bytes) return DPG_OK;
   if (ctx.external_memory) {
     ctx.last_error = "lent scratch too small";
     return DPG_ENOMEM;
   }
+  if (injected_failure(ctx)) return DPG_ENOMEM;
   const size_t grain = size_t(2) << 20;
   const size_t want = (bytes + grain - 1) / grain * grain;
   if (ctx.scratch) {
@@ -125,6 +135,7 @@ int ensure_aux(dpg_ctx& ctx, size_t bytes) {
     ctx.last_error = "lent work space too small";
     return DPG_ENOMEM;
   }
+  if (injected_failure(ctx)) return DPG_ENOMEM;
   const size_t grain = size_t(2) << 20;
   const size_t want = (bytes + grain - 1) / grain * grain;
   if (ctx.aux) {
@@ -176,8 +187,10 @@ dpg_status dpg_ctx_create(dpg_ctx** out, int device) {
   int smem = 0;
   if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
-      cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess ||
-      cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+      cudaDeviceGetAttribute(&c->sm_khz, cudaDevAttrClockRate, device) != cudaSuccess ||
+      cudaMalloc(&c->d_err, dpg::kErrBlockBytes) != cudaSuccess ||
+      cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->d_err, 0, dpg::kErrBlockBytes) != cudaSuccess) {
     cudaGetLastError();
     if (c->d_err) cudaFree(c->d_err);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -210,6 +223,26 @@ void dpg_ctx_destroy(dpg_ctx* c) {
 }
 
 const char* dpg_last_error(dpg_ctx* c) { return c ? c->last_error.c_str() : ""; }
+
+dpg_status dpg_set_wait_limit(dpg_ctx* c, double seconds) {
+  if (!c || !(seconds > 0.0) || seconds > 60.0) return DPG_EINVAL;
+  const double khz = c->sm_khz > 0 ? (double)c->sm_khz : 2.07e6;
+  c->wait_cycles = std::max<long long>(1, (long long)(seconds * khz * 1e3));
+  return DPG_OK;
+}
+
+dpg_status dpg_check_wait(dpg_ctx* c, void* stream) {
+  if (!c) return DPG_EINVAL;
+  DeviceGuard g(c->device);
+  const uint32_t* never = reinterpret_cast<const uint32_t*>(c->d_err) + dpg::kErrNeverSetWord;
+  return (dpg_status)dpg::launch_wait_check(*c, never, static_cast<cudaStream_t>(stream));
+}
+
+dpg_status dpg_inject_alloc_failure(dpg_ctx* c, int count) {
+  if (!c || count < 0) return DPG_EINVAL;
+  c->fail_allocs = count;
+  return DPG_OK;
+}
 
 uint64_t dpg_kernel_launches(dpg_ctx* c) { return c ? c->launches : 0; }
 
@@ -424,6 +457,7 @@ dpg_status dpg_trace_get(dpg_ctx* c, size_t index, const char** name, double* to
 
 static int ensure_io(dpg_ctx& c, size_t bytes) {
   if (bytes <= c.io_bytes) return DPG_OK;
+  if (dpg::injected_failure(c)) return DPG_ENOMEM;
   if (c.io) {
     cudaFree(c.io);
     c.io = nullptr;

@@ -9,16 +9,25 @@ namespace dpg {
 // Bits of the context's device error word.
 enum : int { ERR_RANGE = 1, ERR_TIMEOUT = 2 };
 
-// Bounded device-side waits give up after this many SM clock cycles (~1 s).
+// Bounded device-side waits give up after this many SM clock cycles unless
+// the context sets another limit (about 1 s at the 2.07 GHz SM clock).
 constexpr long long kWaitCycles = 2000000000LL;
 
-// q = n / d by a 64-bit multiply-high with m = ceil(2^64 / d).  Exact whenever
-// n * d < 2^64 (the error n * (m - 2^64/d) / 2^64 stays below 1/d); here
-// n < 2^48 and d < 2^17.  d == 1 is handled apart because m would be 2^64.
+// q = n / d by a 64-bit multiply-high with m = ceil(2^64 / d) = (2^64 + e) / d,
+// 0 <= e < d.  Then n * m / 2^64 = n / d + n * e / (d * 2^64), and the floor
+// is exact whenever n * e < 2^64, so whenever n * d < 2^64.  The launches
+// divide word indices t < n * W by W = rec / WB (n < 2^31, W <= 2^16: t * W
+// < 2^63) and join-row word indices by the row's word count, for which the
+// join entry point checks the bound.  make_fastdiv(d, n_end) states the
+// largest dividend + 1 a launch will use and reports, in `exact`, whether
+// every n < n_end divides exactly; launches refuse to run when it does not.
+// d == 1 is handled apart because m would be 2^64.
 struct FastDiv {
   uint64_t m;
   uint32_t d;
 };
+
+inline bool fastdiv_exact(uint32_t d, uint64_t n_end) { return d <= 1 || n_end <= UINT64_MAX / d; }
 
 inline FastDiv make_fastdiv(uint32_t d) {
   FastDiv f;
@@ -173,13 +182,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of `bar`, giving up after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  long long t0 = clock64();
+// Wait for phase `parity` of `bar`, giving up after `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
+}
+
+// Wait until the 32-bit word at p satisfies `done(value)`, giving up after
+// `limit` SM cycles; returns the last value read and sets *ok.  Every wait on
+// a flag written by another CTA goes through here, so one limit (the
+// context's) bounds them all.
+template <class Done>
+__device__ __forceinline__ uint32_t wait_word_bounded(const uint32_t* p, long long limit, bool* ok, Done done) {
+  const volatile uint32_t* v = p;
+  const long long t0 = clock64();
+  uint32_t x = *v;
+  while (!done(x)) {
+    if (clock64() - t0 > limit) {
+      *ok = false;
+      return x;
+    }
+    __nanosleep(32);
+    x = *v;
+  }
+  *ok = true;
+  return x;
 }
 
 }  // namespace dpg

@@ -17,6 +17,9 @@ struct dpg_ctx {
   int sms = 0;
   size_t smem_optin = 0;     // max dynamic shared memory per block (opt-in)
   int* d_err = nullptr;      // device error word (bits dpg::ERR_*)
+  long long wait_cycles = 2000000000LL;  // limit of device waits on other CTAs' flags (SM cycles)
+  int sm_khz = 0;            // SM clock rate, to turn dpg_set_wait_limit's time into cycles
+  int fail_allocs = 0;       // allocations left to fail (dpg_inject_alloc_failure)
   int* h_err = nullptr;      // pinned host copy used by dpg_sync
   void* scratch = nullptr;   // grown on demand
   size_t scratch_bytes = 0;
@@ -109,6 +112,16 @@ struct Retrieval {
   cudaStream_t stream;
   const JoinSpec* join = nullptr;
 };
+
+// The context's device error block: word 0 is the error word (bits
+// dpg::ERR_*); word kErrNeverSetWord, on a line of its own, stays zero for
+// ever (the flag dpg_check_wait waits on).
+constexpr size_t kErrBlockBytes = 256;
+constexpr size_t kErrNeverSetWord = 32;
+
+// One kernel waiting, under ctx.wait_cycles, for *flag to become non-zero
+// (dpg_check_wait; dpg_retrieve.cu).
+int launch_wait_check(dpg_ctx& ctx, const uint32_t* flag, cudaStream_t st);
 
 // Limits of the DPG path.
 constexpr uint32_t kMaxDpgRecBytes = 65536;   // a segment holds at least one record

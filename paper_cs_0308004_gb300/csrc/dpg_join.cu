@@ -69,6 +69,11 @@ extern "C" dpg_status dpg_fk_join(dpg_ctx* c, const void* fact_v, size_t n_fact,
   if (n_fact > 0x7fffffffULL || n_dim > 0x7fffffffULL || fact_bytes > kMaxDpgRecBytes ||
       dim_bytes > kMaxDpgRecBytes)
     return DPG_EINVAL;
+  // join rows are walked as word indices t < n_fact * row_w divided by the
+  // row's word count row_w (at most (fact_bytes + dim_bytes) one-byte words):
+  // the multiply-high division is exact only while t * row_w < 2^64
+  if (!fastdiv_exact((uint32_t)(fact_bytes + dim_bytes), (uint64_t)n_fact * (fact_bytes + dim_bytes)))
+    return DPG_EINVAL;
   if (n_fact == 0) return DPG_OK;
   if (!fact_v || !out_v || (n_dim && !dim_v) || reinterpret_cast<uintptr_t>(fact_v) % 4) return DPG_EINVAL;
   const size_t out_bytes = n_fact * (fact_bytes + dim_bytes);

@@ -302,7 +302,9 @@ __global__ void __launch_bounds__(kProbeThreads)
   T* ow = reinterpret_cast<T*>(out);
   for (;;) {
     if (threadIdx.x == 0) {
-      const uint32_t it = atomicAdd(item_counter, 1u);
+      // once any CTA has raised an error no further item is taken, so no
+      // further bulk copy is issued
+      const uint32_t it = error_set(err) ? n_items : atomicAdd(item_counter, 1u);
       s_item = it;
       if (it < n_items) {
         uint32_t a = 0, z = nb;  // first j with itemoff[j] > it; itemoff[0] = 0 <= it
@@ -350,11 +352,18 @@ __global__ void __launch_bounds__(kProbeThreads)
         if (SCATTER) dest_s[q] = dest[q0 + q];
       }
       if (wait_bulk) {
-        const bool ok = mbar_wait_bounded(&bar, phase);
+        // The copy is this CTA's own global -> shared bulk copy of at most
+        // 104 KB, which lands within microseconds on a working device; the
+        // bound only guards against a device that has stopped.  If it runs
+        // out, thread 0 records the timeout and waits once more (bounded
+        // again) for the copy already issued, so that the CTA does not
+        // release shared memory the copy may still write; no other copy is
+        // issued after the error bit is set (see the item claim above).
+        const bool ok = mbar_wait_bounded(&bar, phase, kWaitCycles);
         if (__syncthreads_or(!ok)) {
           if (threadIdx.x == 0) {
             atomicOr(err, ERR_TIMEOUT);
-            mbar_wait_bounded(&bar, phase);  // let the copy in flight land before exiting
+            mbar_wait_bounded(&bar, phase, 4 * kWaitCycles);
           }
           return;
         }
@@ -546,6 +555,14 @@ void launch_join_rows(dpg_ctx& ctx, const char* name, uint32_t WB, const uint8_t
 
 // Sets the range bit when n > 0 rids address an empty source table.
 __global__ void k_flag_range(int* err) { atomicOr(err, ERR_RANGE); }
+
+// dpg_check_wait: one thread waits for *flag to become non-zero under the
+// context's limit and records the timeout when it runs out.
+__global__ void k_wait_check(const uint32_t* flag, int* err, long long limit) {
+  bool ok;
+  wait_word_bounded(flag, limit, &ok, [](uint32_t x) { return x != 0; });
+  if (!ok) atomicOr(err, ERR_TIMEOUT);
+}
 
 // ------------------------------------------------------------------ host side
 
@@ -889,6 +906,14 @@ int run_dpg(dpg_ctx& ctx, const Retrieval& r, const Plan& plan) {
   return lo16 ? run_dpg_t<RidStrided, uint16_t>(ctx, r, s, plan) : run_dpg_t<RidStrided, uint32_t>(ctx, r, s, plan);
 }
 
+int launch_wait_check(dpg_ctx& ctx, const uint32_t* flag, cudaStream_t st) {
+  TraceScope ts(ctx, "k_wait_check", st);
+  k_wait_check<<<1, 1, 0, st>>>(flag, ctx.d_err, ctx.wait_cycles);
+  ctx.launches++;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "wait check launch");
+}
+
 int run_join_direct(dpg_ctx& ctx, const JoinSpec& j, uint64_t n_fact, cudaStream_t st) {
   if (n_fact == 0) return DPG_OK;
   const uint32_t wb = std::min({pow2_align(j.fact_bytes), pow2_align(j.dim_bytes),
@@ -967,7 +992,10 @@ unsigned char* g_noalloc_ptr[kNoallocDevices] = {};
 int g_noalloc_sms[kNoallocDevices] = {};
 
 // Device address of the array for the current device, looked up on the first
-// call made with that device current.
+// call made with that device current.  That lookup is also what makes the
+// runtime load this file's device code on the device when nothing else of the
+// library has run there yet (lazy module loading), and loading the module is
+// when the array is reserved: the first call is the set-up call.
 int noalloc_setup(int dev, unsigned char** out, int* sms) {
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {

@@ -93,7 +93,8 @@ constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kCountMask = (1u
 template <class E>
 __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
     k_rs_onesweep(const E* __restrict__ in, E* __restrict__ out, uint64_t n, uint32_t byte,
-                  const uint32_t* __restrict__ digit_count, uint32_t* status, uint32_t* tile_ctr, int* err) {
+                  const uint32_t* __restrict__ digit_count, uint32_t* status, uint32_t* tile_ctr, int* err,
+                  long long wait_limit) {
   __shared__ uint16_t whist[kRsWarps][256];
   __shared__ uint32_t wmask[kRsWarps][256];  // lanes of a warp holding digit d in this round
   __shared__ uint32_t tcnt[256], toff[256], s_base[256], s_excl[256];
@@ -179,21 +180,18 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
     st[(uint64_t)t * 256 + dg] = (t == 0 ? kFlagPrefix : kFlagAgg) | run;
     uint32_t excl = 0;
     if (t > 0) {
-      int64_t j = (int64_t)t - 1;
-      const long long t0 = clock64();
-      while (j >= 0) {
-        const uint32_t w = st[(uint64_t)j * 256 + dg];
-        const uint32_t flag = w & ~kCountMask;
-        if (flag == 0) {
-          if (clock64() - t0 > kWaitCycles) {
-            atomicOr(err, ERR_TIMEOUT);
-            break;
-          }
-          continue;
+      // tile j < t was claimed before this one, so its CTA is running and
+      // publishes its count; the wait is bounded all the same
+      for (int64_t j = (int64_t)t - 1; j >= 0; --j) {
+        bool ok;
+        const uint32_t w = wait_word_bounded(status + (uint64_t)j * 256 + dg, wait_limit, &ok,
+                                             [](uint32_t x) { return (x & ~kCountMask) != 0; });
+        if (!ok) {
+          atomicOr(err, ERR_TIMEOUT);
+          break;
         }
         excl += w & kCountMask;
-        if (flag == kFlagPrefix) break;
-        --j;
+        if ((w & ~kCountMask) == kFlagPrefix) break;
       }
       st[(uint64_t)t * 256 + dg] = kFlagPrefix | (excl + run);
     }
@@ -279,7 +277,7 @@ uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint
     {
       TraceScope ts(ctx, "k_rs_onesweep", st);
       k_rs_onesweep<E><<<ntiles, kRsThreads, smem, st>>>(a, b, n, (uint32_t)byte, counts + 256 * byte, tile_status,
-                                                        tile_ctr, ctx.d_err);
+                                                        tile_ctr, ctx.d_err, ctx.wait_cycles);
     }
     ctx.launches++;
     std::swap(a, b);

@@ -56,6 +56,9 @@ SIGNATURES = {
     "dpg_server_destroy": ([_P], None),
     "dpg_tune": ([_P, _P, _S, _S, _S, _P, _S, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "dpg_last_plan": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I)], None),
+    "dpg_set_wait_limit": ([_P, ctypes.c_double], _I),
+    "dpg_check_wait": ([_P, _P], _I),
+    "dpg_inject_alloc_failure": ([_P, _I], _I),
 }
 
 JOIN_MODES = {"move": 0, "sort": 1, "direct": 2}
@@ -169,6 +172,19 @@ class Context:
     @property
     def kernel_launches(self) -> int:
         return int(lib.dpg_kernel_launches(self._h))
+
+    # -- failure detection
+    def set_wait_limit(self, seconds: float):
+        """Limit of every device wait on another CTA's flag (seconds of SM clock)."""
+        self._check(lib.dpg_set_wait_limit(self._h, float(seconds)), "dpg_set_wait_limit")
+
+    def check_wait(self, stream=None):
+        """Enqueue one bounded wait on a flag nothing sets (the next sync reports the timeout)."""
+        self._check(lib.dpg_check_wait(self._h, _stream_handle(stream, self.device)), "dpg_check_wait")
+
+    def inject_alloc_failure(self, count: int = 1):
+        """Make the next `count` device allocations of this context fail (DPG_ENOMEM)."""
+        self._check(lib.dpg_inject_alloc_failure(self._h, int(count)), "dpg_inject_alloc_failure")
 
     # -- operations
     def _retrieve(self, fn, src, rids, out, stream):

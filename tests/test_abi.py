@@ -53,3 +53,10 @@ def test_host_side_argument_errors(lib):
     assert lib.dpg_sync(None, None) == 1
     lib.dpg_ctx_create.argtypes = [ctypes.c_void_p, ctypes.c_int]
     assert lib.dpg_ctx_create(None, 0) == 1
+    # failure-detection hooks refuse a null context on the host as well
+    lib.dpg_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    assert lib.dpg_set_wait_limit(None, 1.0) == 1
+    lib.dpg_check_wait.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.dpg_check_wait(None, None) == 1
+    lib.dpg_inject_alloc_failure.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.dpg_inject_alloc_failure(None, 1) == 1

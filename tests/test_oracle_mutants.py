@@ -1,7 +1,8 @@
 """Plant plausible mistakes in copies of the oracle and check the pins catch them.
 
 Each mutant is oracle.c with one textual change (a dropped byte, a wrong index,
-an off-by-one range check, a cursor that does not advance, a reversed tie order,
+an off-by-one range check, a dropped rank or run start in the three-phase
+statement, a reversed tie order,
 a shortened key, a neighbouring dimension row, a reversed join order), compiled
 into a temporary library and swapped in; at least one pin must then fail.
 """
@@ -23,13 +24,17 @@ MUTANTS = {
                        "memcpy(dst + i * rec, src + (uint64_t)rids[n - 1 - i] * rec, rec);"),
     "range_off_by_one": ("if (rids[i] < 0 || (uint64_t)rids[i] >= n_src) return OR_ERANGE;\n  for (uint64_t i = 0; i < n; ++i)\n    memcpy",
                          "if (rids[i] < 0 || (uint64_t)rids[i] > n_src) return OR_ERANGE;\n  for (uint64_t i = 0; i < n; ++i)\n    memcpy"),
-    "gather_cursor_stuck": ("    next[j]++;\n", "\n"),
-    "probe_wrong_run": ("memcpy(internal_run[j] + k * rec, src + (uint64_t)run[j][k] * rec, rec);",
-                        "memcpy(internal_run[j] + k * rec, src + (uint64_t)run[j][len[j] - 1 - k] * rec, rec);"),
+    "gather_rank_dropped": ("      if ((uint64_t)rids[m] / L == j) rank++;", "      ;"),
+    "probe_wrong_entry": ("memcpy(internal + k * rec, src + (uint64_t)rid_runs[k] * rec, rec);",
+                          "memcpy(internal + k * rec, src + (uint64_t)rid_runs[n - 1 - k] * rec, rec);"),
+    "run_start_off_by_one": ("for (uint64_t m = 0; m < j; ++m) start += run_sizes[m];",
+                             "for (uint64_t m = 0; m + 1 < j; ++m) start += run_sizes[m];"),
     "tie_order_reversed": ("return (ra > rb) - (ra < rb);", "return (ra < rb) - (ra > rb);"),
     "short_key": ("int c = memcmp(a, b, g_key_bytes);", "int c = memcmp(a, b, g_key_bytes - 1);"),
     "neighbour_dim_row": ("memcpy(out + i * w + fact_bytes, dim + (uint64_t)fk * dim_bytes, dim_bytes);",
                           "memcpy(out + i * w + fact_bytes, dim + (uint64_t)(fk > 0 ? fk - 1 : 0) * dim_bytes, dim_bytes);"),
+    "order_ties_reversed": ("for (uint64_t i = 0; i < n_fact; ++i) order[",
+                            "for (uint64_t i = n_fact; i-- > 0;) order["),
     "join_order_reversed": ("if (x->fk != y->fk) return (x->fk > y->fk) - (x->fk < y->fk);",
                             "if (x->fk != y->fk) return (x->fk < y->fk) - (x->fk > y->fk);"),
 }
@@ -48,6 +53,7 @@ PIN_CALLS = [
     lambda: pins.test_sort_records_sorted_file(),
     lambda: pins.test_fk_join_move_equals_nested(50, 400),
     lambda: pins.test_fk_join_sorted_order(50, 400),
+    lambda: pins.test_fk_join_order_is_the_sorted_join(50, 400),
 ]
 
 

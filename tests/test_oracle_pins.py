@@ -304,6 +304,21 @@ def test_fk_join_sorted_order(n_dim, n_fact):
     assert np.array_equal(srt, nested[order])
 
 
+@pytest.mark.parametrize("n_dim,n_fact", [(1, 5), (7, 300), (50, 400), (1000, 20_000)])
+def test_fk_join_order_is_the_sorted_join(n_dim, n_fact):
+    """The linear-time join order (stable counting sort) against the
+    comparison sort of oracle_fk_join_sorted and a brute-force (fk, row)
+    ordering: rows of the sorted join are move-join rows of fact[order]."""
+    dim, fact, fk = _fk_case(n_dim, n_fact, 11 + n_dim)
+    order = oracle.fk_join_order(fact, n_dim)
+    assert order.tolist() == sorted(range(n_fact), key=lambda i: (int(fk[i]), i))
+    assert np.array_equal(oracle.fk_join_move(fact[order], dim), oracle.fk_join_sorted(fact, dim))
+    bad = fact.copy()
+    bad[n_fact // 2, :4] = np.array([n_dim], "<i4").view(np.uint8)
+    with pytest.raises(oracle.OracleRangeError):
+        oracle.fk_join_order(bad, n_dim)
+
+
 def test_fk_join_bad_key():
     dim, fact, fk = _fk_case(10, 30, 9)
     fact[3, :4] = np.array([10], "<i4").view(np.uint8)

@@ -1,7 +1,7 @@
 """Parity of the GPU three-phase sort (§3) with the oracle, byte for byte:
 key-pointer pairs (dpg_sort_keyptr) and sorted records (dpg_sort_records),
-over ragged tile counts, record sizes, key lengths, ties, and the full-size
-10,000,000 x 100-byte file."""
+over ragged tile counts, record sizes, key lengths and ties (the full-size
+10,000,000 x 100-byte file is compared row by row in test_full_size_gpu.py)."""
 import numpy as np
 import pytest
 import torch
@@ -63,23 +63,6 @@ def test_sort_records_matches_oracle(ctx, monkeypatch, rec, variant):
     got = ctx.sort_records(to_dev(src), 10)
     ctx.sync()
     assert np.array_equal(got.cpu().numpy(), oracle.sort_records(src, 10))
-
-
-def test_sort_full_size(ctx):
-    """10,000,000 records of 100 bytes: every pair against the oracle, the
-    sorted file sampled against the oracle's sort copy."""
-    n, rec = 10_000_000, 100
-    src = synth.sort_file(n, rec, 3)
-    want_pairs = oracle.sort_keyptr(src, 10)
-    d_src = to_dev(src)
-    got = ctx.sort_keyptr(d_src, 10)
-    ctx.sync()
-    assert torch.equal(got, to_dev(want_pairs))
-    out = ctx.sort_records(d_src, 10)
-    ctx.sync()
-    idx = np.sort(synth.uniform_ids(50_000, n, 3)).astype(np.int64)
-    want = oracle.retrieve(src, oracle.pair_rids(want_pairs)[idx])
-    assert np.array_equal(out[torch.from_numpy(idx).to(DEV)].cpu().numpy(), want)
 
 
 def test_sort_argument_errors(ctx):

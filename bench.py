@@ -420,9 +420,10 @@ def run_batch(a):
         cur_bytes += b
     if cur:
         waves.append(cur)
-    tot_ms = tot_ms_direct = 0.0
+    tot = {"exec": 0.0, "grouped": 0.0}
+    tot_ms_direct = 0.0
     alg = 0
-    launches = []
+    launches = {}
     tuned = {}
     for wave in waves:
         reqs, groups = [], []
@@ -446,27 +447,34 @@ def run_batch(a):
             v_, sl_ = ctx.tune(tables[r_], d_rids_, arena_)
             tuned.setdefault(r_, {}).setdefault(f"{v_}/{sl_}", 0)
             tuned[r_][f"{v_}/{sl_}"] += 1
-        ctx.retrieve_batch(reqs)                      # warm-up sizes the work space
-        ctx.sync()
-        s = torch.cuda.Stream(dev)
-        g = torch.cuda.CUDAGraph()
-        l0 = ctx.kernel_launches
-        with torch.cuda.stream(s):
-            with torch.cuda.graph(g, stream=s):
-                ctx.retrieve_batch(reqs, stream=s)
-        launches.append(ctx.kernel_launches - l0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record()
-        for _ in range(a.steps):
-            g.replay()
-        e1.record()
-        torch.cuda.synchronize(dev)
-        ctx.sync()
-        tot_ms += e0.elapsed_time(e1) / a.steps
-        for r, d_rids, arena in groups:            # spot check each group
-            idx = torch.randint(0, d_rids.numel(), (1024,), device=dev)
-            assert torch.equal(arena[idx], tables[r][d_rids[idx].long()])
+        # the wave as one captured graph, by the persistent executor (the
+        # default) and by the grouped multi-kernel path
+        for mode in ("exec", "grouped"):
+            if mode == "grouped":
+                os.environ["DPG_BATCH_GROUPED"] = "1"
+            ctx.retrieve_batch(reqs)                  # warm-up sizes the work space
+            ctx.sync()
+            s = torch.cuda.Stream(dev)
+            g = torch.cuda.CUDAGraph()
+            l0 = ctx.kernel_launches
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g, stream=s):
+                    ctx.retrieve_batch(reqs, stream=s)
+            launches.setdefault(mode, []).append(ctx.kernel_launches - l0)
+            os.environ.pop("DPG_BATCH_GROUPED", None)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record()
+            for _ in range(a.steps):
+                g.replay()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ctx.sync()
+            tot[mode] += e0.elapsed_time(e1) / a.steps
+            for r, d_rids, arena in groups:            # spot check each group
+                idx = torch.randint(0, d_rids.numel(), (1024,), device=dev)
+                assert torch.equal(arena[idx], tables[r][d_rids[idx].long()])
+            del g
         e0.record()
         for _ in range(a.steps):
             for r, d_rids, arena in groups:
@@ -475,16 +483,21 @@ def run_batch(a):
         torch.cuda.synchronize(dev)
         ctx.sync()
         tot_ms_direct += e0.elapsed_time(e1) / a.steps
-        del g, reqs, groups
+        del reqs, groups
         torch.cuda.empty_cache()
+    tot_ms = tot["exec"]
     print(json.dumps({"impl": "batch", "requests": int(n.size), "records": int(n.sum()),
                       "dst_bytes": int((n * rec).sum()), "waves": len(waves), "wave_budget_gb": a.wave_gb,
                       "algorithmic_bytes": alg, "steps": a.steps, "input_generation_s": round(t_gen, 1),
                       "dpg_batch_ms": round(tot_ms, 3), "dpg_batch_gbs": round(alg / tot_ms / 1e6, 1),
                       "dpg_pct_of_hbm_peak": round(alg / tot_ms / 1e6 / peak, 4),
+                      "dpg_batch_path": "persistent executor: one persistent launch per DPG phase per wave",
+                      "grouped_ms": round(tot["grouped"], 3), "grouped_gbs": round(alg / tot["grouped"] / 1e6, 1),
                       "direct_ms": round(tot_ms_direct, 3), "direct_gbs": round(alg / tot_ms_direct / 1e6, 1),
                       "speedup_vs_direct": round(tot_ms_direct / tot_ms, 4),
-                      "kernels_per_wave_graph": launches, "peak": peak, "peak_kind": peak_kind,
+                      "grouped_speedup_vs_direct": round(tot_ms_direct / tot["grouped"], 4),
+                      "kernels_per_wave_graph": launches.get("exec"),
+                      "grouped_kernels_per_wave_graph": launches.get("grouped"), "peak": peak, "peak_kind": peak_kind,
                       "tuned_plans": {str(r_): v_ for r_, v_ in sorted(tuned.items())},
                       "tuning": "dpg_tune per (wave, record size) group, outside the timed region; "
                                 "plans as variant/seg_log2 with the number of groups that took each"}),

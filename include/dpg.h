@@ -156,17 +156,16 @@ dpg_status dpg_fk_join(dpg_ctx* ctx, const void* fact, size_t n_fact, size_t fac
 /*
  * Batched retrieval: `count` requests (a HOST array; its pointers are device
  * pointers), each dst_k[i] = src_k[rids_k[i]] as in dpg_retrieve, with uneven
- * record counts and record sizes.  Requests that read the same source table
- * with the same record size are retrieved together as one DPG run over their
- * concatenated rid lists, so each source segment is probed once per group
- * (each rid is still checked against its own request's n_src).  Fastest when
- * the requests of a group have their rids back to back in one array and their
- * destinations back to back in one buffer (in request order); otherwise the
- * call assembles and scatters them in its work space.  Stream-ordered: after
- * one warm-up call at the same sizes, a batch can be captured in a CUDA graph
- * (the request table is staged in context-owned pinned memory that a replay
- * reads again: do not issue other batches on the context between capture and
- * replay).  The first error of any request is reported by dpg_sync.
+ * record counts and record sizes: dpg_run_batch (below) with every request a
+ * retrieval item.  Requests that read the same source table with the same
+ * record size are retrieved together by one DPG pass, so each run of the
+ * table is probed once per group (each rid is still checked against its own
+ * request's n_src).  Stream-ordered: after one warm-up call at the same
+ * sizes, a batch can be captured in a CUDA graph (the request tables are
+ * staged in context-owned pinned memory that a replay reads again: do not
+ * issue other batches on the context between capture and replay).  A bad rid
+ * in any request leaves every destination untouched and is reported by
+ * dpg_sync.
  */
 typedef struct dpg_request {
   const void* src;      /* n_src records of rec_bytes bytes */
@@ -213,6 +212,39 @@ typedef struct dpg_job {
   size_t dim_bytes;
   size_t pk_off;
 } dpg_job;
+
+/*
+ * Batch execution (§2.1 and §4.2.1 for many requests at once; the paper has
+ * no batch layer).  `count` items (a HOST array; its pointers are device
+ * pointers), each a retrieval (job.kind DPG_JOB_RETRIEVE: out[i] =
+ * src[rids[i]], n records of rec_bytes) or a DPG-move join (job.kind
+ * DPG_JOB_JOIN, job.join_mode DPG_JOIN_MOVE: out row i = fact[i] ||
+ * dim[fk_i], the layout rules of dpg_fk_join), of uneven sizes, run by a
+ * persistent executor over a device table of work items (request group, DPG
+ * phase, chunk) that its CTAs claim in order: one persistent launch per DPG
+ * phase (four in stream order), or, with the environment variable
+ * DPG_EXEC_FUSED=1, all four phases in ONE persistent launch where an item
+ * waits, with the context's wait limit (dpg_set_wait_limit), only for items
+ * claimed before it.  Retrievals reading the same source table with the same record size
+ * share one DPG pass over the L2-resident runs of that table (each rid is
+ * still checked against its own n_src); a join is a group of its own.  Per
+ * group the plan is the L2-run plan through INTERNAL below 192-byte records
+ * and for joins, and the fused plan that writes each record straight to its
+ * destination from 192 bytes, unless dpg_tune cached a plan for the group's
+ * shape.  Before anything is written every rid of every item is checked: a
+ * bad rid or key anywhere leaves every destination untouched and dpg_sync
+ * returns DPG_ERANGE (a dimension row whose key differs from its row number
+ * is found later, as in dpg_fk_join).  Work space comes from the context (one
+ * warm-up call at the same sizes before a CUDA-graph capture; the item
+ * tables are staged in context-owned pinned memory that a replay reads
+ * again).  Argument errors return DPG_EINVAL with nothing enqueued.
+ */
+typedef struct dpg_batch_item {
+  dpg_job job;
+  void* out;            /* n records, or n_fact join rows of fact_bytes + dim_bytes */
+} dpg_batch_item;
+
+dpg_status dpg_run_batch(dpg_ctx* ctx, const dpg_batch_item* items, size_t count, void* stream);
 
 dpg_status dpg_server_create(dpg_server** out, int device, int slots, size_t budget_bytes);
 /* Queue a job; *ticket identifies it.  DPG_EINVAL for a malformed job,

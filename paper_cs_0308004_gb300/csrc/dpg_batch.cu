@@ -16,6 +16,7 @@
 
 #include "dpg_device.cuh"
 #include "dpg_internal.h"
+#include "dpg_launch.cuh"
 
 namespace dpg {
 namespace {
@@ -110,6 +111,27 @@ inline uint32_t align_of(uint64_t x) {
 extern "C" dpg_status dpg_retrieve_batch(dpg_ctx* c, const dpg_request* reqs, size_t count, void* stream) {
   using namespace dpg;
   if (!c || (count && !reqs)) return DPG_EINVAL;
+  if (env_int("DPG_BATCH_GROUPED", 0) == 0) {
+    // the persistent executor: every request a retrieval item
+    std::vector<dpg_batch_item> items(count);
+    for (size_t k = 0; k < count; ++k) {
+      dpg_batch_item& it = items[k];
+      std::memset(&it, 0, sizeof it);
+      it.job.kind = DPG_JOB_RETRIEVE;
+      it.job.src = reqs[k].src;
+      it.job.n_src = reqs[k].n_src;
+      it.job.rec_bytes = reqs[k].rec_bytes;
+      it.job.n = reqs[k].n;
+      it.job.rids = reqs[k].rids;
+      it.out = reqs[k].dst;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != c->device) cudaSetDevice(c->device);
+    const int s = run_exec_batch(*c, items.data(), count, static_cast<cudaStream_t>(stream));
+    if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
+    return (dpg_status)s;
+  }
   // host-side checks of every request, before anything is enqueued
   std::vector<size_t> live;
   for (size_t k = 0; k < count; ++k) {

@@ -159,6 +159,11 @@ void launch_slot_gather(dpg_ctx& ctx, uint32_t wb, const uint8_t* src, uint8_t* 
 // (dpg_retrieve.cu).
 void launch_join_phase3(dpg_ctx& ctx, const Retrieval& r, const uint8_t* stage, const uint32_t* slot);
 
+// The batch executor (dpg_exec.cu): every item of a batch as one persistent
+// kernel; the grouped multi-kernel batch (dpg_batch.cu) runs instead when
+// DPG_BATCH_GROUPED=1.
+int run_exec_batch(dpg_ctx& ctx, const dpg_batch_item* items, size_t count, cudaStream_t st);
+
 // Scratch arena helpers (dpg_api.cu).
 int ensure_scratch(dpg_ctx& ctx, size_t bytes);
 int ensure_aux(dpg_ctx& ctx, size_t bytes);

@@ -56,6 +56,7 @@ SIGNATURES = {
     "dpg_server_destroy": ([_P], None),
     "dpg_tune": ([_P, _P, _S, _S, _S, _P, _S, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "dpg_last_plan": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I)], None),
+    "dpg_run_batch": ([_P, _P, _S, _P], _I),
     "dpg_set_wait_limit": ([_P, ctypes.c_double], _I),
     "dpg_check_wait": ([_P, _P], _I),
     "dpg_inject_alloc_failure": ([_P, _I], _I),
@@ -72,6 +73,11 @@ class Job(ctypes.Structure):
                 ("fact", ctypes.c_void_p), ("n_fact", ctypes.c_size_t), ("fact_bytes", ctypes.c_size_t),
                 ("fk_off", ctypes.c_size_t), ("dim", ctypes.c_void_p), ("n_dim", ctypes.c_size_t),
                 ("dim_bytes", ctypes.c_size_t), ("pk_off", ctypes.c_size_t)]
+
+
+class BatchItem(ctypes.Structure):
+    """struct dpg_batch_item (include/dpg.h)."""
+    _fields_ = [("job", Job), ("out", ctypes.c_void_p)]
 
 
 class Request(ctypes.Structure):
@@ -299,6 +305,42 @@ class Context:
         st = lib.dpg_retrieve_batch(self._h, ctypes.cast(arr, ctypes.c_void_p), len(requests),
                                     _stream_handle(stream, self.device))
         self._check(st, "dpg_retrieve_batch")
+
+    def run_batch(self, items, stream=None):
+        """One persistent launch over a batch of retrievals and DPG-move joins.
+        items: ("retrieve", src, rids, out[, n_src]) or ("join", fact, dim, out[, fk_off, pk_off]),
+        device tensors.  Asynchronous; call sync()."""
+        arr = (BatchItem * max(1, len(items)))()
+        for k, it in enumerate(items):
+            if it[0] == "retrieve":
+                src, rids, out = it[1:4]
+                n_src = it[4] if len(it) > 4 else src.shape[0]
+                for t, nm in ((src, "src"), (rids, "rids"), (out, "out")):
+                    _need_cuda(t, nm, self.device)
+                _, rec = _table(src, "src")
+                if rids.dtype != torch.int32 or tuple(out.shape) != (rids.shape[0], rec) or out.dtype != torch.uint8:
+                    raise ValueError("a retrieval needs int32 rids and a uint8 out of shape (len(rids), record bytes)")
+                arr[k].job = Job(kind=0, src=src.data_ptr(), n_src=n_src, rec_bytes=rec, n=rids.shape[0],
+                                 rids=rids.data_ptr())
+            elif it[0] == "join":
+                fact, dim, out = it[1:4]
+                fk_off = it[4] if len(it) > 4 else 0
+                pk_off = it[5] if len(it) > 5 else 0
+                for t, nm in ((fact, "fact"), (dim, "dim"), (out, "out")):
+                    _need_cuda(t, nm, self.device)
+                n_fact, fb = _table(fact, "fact")
+                n_dim, db = _table(dim, "dim")
+                if tuple(out.shape) != (n_fact, fb + db) or out.dtype != torch.uint8:
+                    raise ValueError("a join needs a uint8 out of shape (fact rows, fact bytes + dim bytes)")
+                arr[k].job = Job(kind=1, join_mode=JOIN_MODES["move"], fact=fact.data_ptr(), n_fact=n_fact,
+                                 fact_bytes=fb, fk_off=fk_off, dim=dim.data_ptr(), n_dim=n_dim, dim_bytes=db,
+                                 pk_off=pk_off)
+            else:
+                raise ValueError(f"unknown batch item kind {it[0]!r}")
+            arr[k].out = out.data_ptr()
+        st = lib.dpg_run_batch(self._h, ctypes.cast(arr, ctypes.c_void_p), len(items),
+                               _stream_handle(stream, self.device))
+        self._check(st, "dpg_run_batch")
 
     def tune(self, src: torch.Tensor, rids: torch.Tensor, out: torch.Tensor | None = None,
              rid_stride: int = 4, rid_off: int = 0, stream=None):

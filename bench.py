@@ -73,7 +73,8 @@ def args_():
                         "rows log-uniform in [1e4, 5e7], record sizes 16..256 B, resident tables, 120 GB "
                         "admission budget; p50/p99 latency and aggregate GB/s; one JSON line")
     p.add_argument("--serve-seconds", type=float, default=10.0)
-    p.add_argument("--serve-rate", type=float, default=2000.0)
+    p.add_argument("--serve-rate", default="1000,2000",
+                   help="mean arrival rates (req/s) of --serve, one JSON line each")
     p.add_argument("--serve-rows", type=int, default=50_000_000)
     p.add_argument("--serve-slots", type=int, default=8)
     p.add_argument("--serve-budget-gb", type=float, default=120.0)
@@ -520,9 +521,17 @@ def run_serve(a):
     d_dim, d_fact = torch.from_numpy(dim).to(dev), torch.from_numpy(fact).to(dev)
     del dim, fact
     t_setup = time.time() - t0
+    for rate in [float(x) for x in str(a.serve_rate).split(",")]:
+        serve_one(a, rate, dev, R, recs, tables, perm, d_dim, d_fact, t_setup)
+
+
+def serve_one(a, rate, dev, R, recs, tables, perm, d_dim, d_fact, t_setup):
+    """One open-loop serving run at `rate` requests per second (see run_serve)."""
+    import torch
+    from paper_cs_0308004_gb300 import dpg
     # the request stream (seed 6): arrival gaps, kind, rows, record size, offset, join mode
-    count = int(a.serve_rate * a.serve_seconds)
-    gaps = -np.log(1.0 - synth.uniform_f64(count, synth.stream_seed(6, 0))) / a.serve_rate
+    count = int(rate * a.serve_seconds)
+    gaps = -np.log(1.0 - synth.uniform_f64(count, synth.stream_seed(6, 0))) / rate
     arrive = np.cumsum(gaps)
     is_join = synth.uniform_f64(count, synth.stream_seed(6, 1)) < 0.4
     u = synth.uniform_f64(count, synth.stream_seed(6, 2))
@@ -597,7 +606,9 @@ def run_serve(a):
     lat_a = np.array(lat)
     offered = sum(job_bytes(k) for k in range(count)) / arrive[-1] / 1e9
     print(json.dumps({"impl": "serve", "requests": count, "seconds_of_arrivals": round(float(arrive[-1]), 2),
-                      "rate_req_s": a.serve_rate, "slots": a.serve_slots, "budget_gb": a.serve_budget_gb,
+                      "rate_req_s": rate, "slots": a.serve_slots, "budget_gb": a.serve_budget_gb,
+                      "admission": "arrival order, a job that fits may pass a waiting head up to "
+                                   f"{os.environ.get('DPG_SERVE_BYPASS', 4 * a.serve_slots)} times",
                       "offered_gbs": round(offered, 1), "aggregate_gbs": round(done_bytes / wall / 1e9, 1),
                       "wall_s": round(wall, 2), "p50_ms": round(float(np.percentile(lat_a, 50)), 3),
                       "p99_ms": round(float(np.percentile(lat_a, 99)), 3), "mean_ms": round(float(lat_a.mean()), 3),

@@ -185,7 +185,11 @@ dpg_status dpg_retrieve_batch(dpg_ctx* ctx, const dpg_request* reqs, size_t coun
  * are queued in submission order; the head of the queue is admitted as soon
  * as a slot is free and the device memory held by running jobs and by results
  * not yet released, plus the job's own work space and result, fits within
- * budget_bytes.  Admitted jobs run concurrently; jobs that arrive while others
+ * budget_bytes.  While the head does not fit, the first later job that does
+ * is admitted ahead of it, at most 4 x slots times per head (the environment
+ * variable DPG_SERVE_BYPASS sets the bound; 0 keeps strict arrival order), so
+ * a large job neither blocks small ones nor starves.  Admitted jobs run
+ * concurrently; jobs that arrive while others
  * run are admitted as slots and memory free up (continuous batching).  A job's
  * tables are device pointers owned by the caller and must stay valid until
  * the job completes; its result is allocated by the server, read with

@@ -5,7 +5,9 @@
 // a context (lent scratch, no device-wide allocation) and a CUDA stream.  Jobs
 // queue in arrival order; the head job is admitted as soon as a slot is free
 // and the memory held by running jobs and unreleased results plus the job's
-// own footprint fits the budget.  Admitted jobs run concurrently on their
+// own footprint fits the budget; when the head does not fit, a later job
+// that does may be admitted ahead of it, at most max_bypass times per head
+// (backfilling with an aging bound).  Admitted jobs run concurrently on their
 // slots' streams.  Device memory comes from a private stream-ordered pool
 // (cudaMallocFromPoolAsync), so admitting or retiring a job never synchronizes
 // the device.  A job's result stays allocated until dpg_server_release.
@@ -20,6 +22,7 @@
 #include <vector>
 
 #include "dpg_internal.h"
+#include "dpg_launch.cuh"
 
 namespace {
 
@@ -37,6 +40,7 @@ struct Job {
   dpg_status status = DPG_OK;
   bool complete = false;
   bool released = false;
+  uint32_t bypassed = 0;  // jobs admitted ahead of this one while it headed the queue
 };
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -58,6 +62,7 @@ struct dpg_server {
   std::thread worker;
   bool stop = false;
   uint64_t next_ticket = 1;
+  uint32_t max_bypass = 0;  // jobs that may be admitted ahead of a queue head that does not fit
 };
 
 namespace {
@@ -178,9 +183,25 @@ void dispatch(dpg_server* s) {
           break;
         }
       if (slot < 0) break;
-      Job& job = *s->jobs[s->queue.front()];
-      if (s->held + job.work_bytes + job.out_bytes > s->budget) break;  // wait for memory (FIFO order kept)
-      s->queue.pop_front();
+      // the head if it fits; else the first queued job that fits, while the
+      // head has been passed fewer than max_bypass times (then the queue
+      // waits for memory in order, so the head is not starved)
+      Job& head = *s->jobs[s->queue.front()];
+      auto fits = [&](const Job& j) { return s->held + j.work_bytes + j.out_bytes <= s->budget; };
+      size_t pick = s->queue.size();
+      if (fits(head)) {
+        pick = 0;
+      } else if (head.bypassed < s->max_bypass) {
+        for (size_t q = 1; q < s->queue.size(); ++q)
+          if (fits(*s->jobs[s->queue[q]])) {
+            pick = q;
+            break;
+          }
+      }
+      if (pick == s->queue.size()) break;  // wait for memory
+      Job& job = *s->jobs[s->queue[pick]];
+      if (pick) head.bypassed++;
+      s->queue.erase(s->queue.begin() + (std::ptrdiff_t)pick);
       s->held += job.work_bytes + job.out_bytes;
       launch(*s, job, slot);
       progress = true;
@@ -261,6 +282,9 @@ dpg_status dpg_server_create(dpg_server** out, int device, int slots, size_t bud
     return rc;
   }
   s->running.assign(slots, 0);
+  // backfilling bound: by default four jobs per slot may pass a head that
+  // waits for memory (DPG_SERVE_BYPASS overrides; 0 keeps strict arrival order)
+  s->max_bypass = (uint32_t)std::max(0, dpg::env_int("DPG_SERVE_BYPASS", 4 * slots));
   s->worker = std::thread(dispatch, s.get());
   if (prev >= 0) cudaSetDevice(prev);
   *out = s.release();

@@ -105,3 +105,49 @@ def test_server_admission_and_errors(workload):
         st, out, _ = srv.result(t)
         assert st == dpg.OK and torch.equal(out, d_tables[16][:1000])
         srv.release(t)
+
+
+@pytest.mark.parametrize("bypass", ["8", "1", "0"])
+def test_server_backfills_past_a_waiting_head(monkeypatch, bypass):
+    """A head job that cannot fit (an earlier result still holds the budget)
+    lets the small jobs behind it run, up to the bypass bound; with the bound
+    at 0 the queue keeps strict arrival order.  Every result matches the
+    oracle once the budget frees up."""
+    import time
+    from paper_cs_0308004_gb300 import dpg
+    monkeypatch.setenv("DPG_SERVE_BYPASS", bypass)
+    n_big, rec = 4_000_000, 256
+    big = synth.records(n_big, rec, 1)
+    big_rids = synth.permutation(n_big, 2)
+    small = synth.records(20_000, 16, 3)
+    small_rids = [synth.uniform_ids(10_000, 20_000, 4 + k) for k in range(2)]
+    d_big, d_big_rids, d_small = to_dev(big), to_dev(big_rids), to_dev(small)
+    d_small_rids = [to_dev(r) for r in small_rids]
+    want_big = oracle.retrieve(big, big_rids)
+    with dpg.Server(0, slots=4, budget_bytes=int(1.5e9)) as srv:
+        t1 = srv.submit_retrieve(d_big, d_big_rids)
+        st, _, _ = srv.result(t1)                 # done; its 1 GB result stays held
+        assert st == dpg.OK
+        t2 = srv.submit_retrieve(d_big, d_big_rids)     # cannot fit until t1 is released
+        t3 = srv.submit_retrieve(d_small, d_small_rids[0])
+        t4 = srv.submit_retrieve(d_small, d_small_rids[1])
+        deadline = time.time() + 3.0
+        done = {}
+        while time.time() < deadline and len(done) < 2:
+            for t in (t3, t4):
+                if t not in done:
+                    r = srv.result(t, wait=False)
+                    if r is not None:
+                        done[t] = r
+            time.sleep(0.01)
+        passed = {"8": {t3, t4}, "1": {t3}, "0": set()}[bypass]
+        assert set(done) == passed
+        assert srv.result(t2, wait=False) is None       # the head still waits for memory
+        srv.release(t1)
+        st, out2, _ = srv.result(t2)
+        assert st == dpg.OK and np.array_equal(out2.cpu().numpy(), want_big)
+        srv.release(t2)
+        for t, rids in ((t3, small_rids[0]), (t4, small_rids[1])):
+            st, out, _ = srv.result(t)
+            assert st == dpg.OK and np.array_equal(out.cpu().numpy(), oracle.retrieve(small, rids))
+            srv.release(t)

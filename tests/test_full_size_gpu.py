@@ -11,7 +11,10 @@ against the oracle (no sampling):
   keys) with 10,000,000 x 64-byte dimension rows (16 GB of output), in all
   three modes, compared in chunks of 10,000,000 rows with oracle.fk_join_move
   (DPG-move, direct) and with the move rows of the fact rows in
-  oracle.fk_join_order's order (DPG-sort).
+  oracle.fk_join_order's order (DPG-sort);
+* the batch of 4096 requests (record counts log-uniform in [1e3, 1.6e7],
+  8..256-byte records, 611 GB of output) in the benchmark's waves, every
+  request against the oracle.
 
 Comparisons run on the device (the oracle's result copied over, then
 compared element by element), so the 1-16 GB outputs need not come back.
@@ -149,3 +152,55 @@ def test_join_full_size_every_row(ctx, monkeypatch, join_case, mode):
         j1 = min(n_fact, j0 + CHUNK)
         rows = fact[j0:j1] if order is None else fact[order[j0:j1]]
         assert_rows_equal(out[j0:j1], oracle.fk_join_move(rows, dim), f"join {mode}, rows {j0}..{j1}", j0)
+
+
+# ---------------------------------------------------------- batched retrieval
+
+def test_batch_full_size_every_request(ctx):
+    """The 4096-request batch (seed 5: 6.9e9 records, 611 GB of output) in
+    waves of at most 48 GB as the benchmark runs it, each wave one
+    dpg_retrieve_batch on the persistent executor; every request's output
+    against the oracle (oracle.retrieve_threads on every host core, pinned to
+    oracle.retrieve by the oracle tests)."""
+    import os
+    n, rec, kind = synth.batch_requests(4096, 1e3, 1.6e7, 5)
+    all_rids, offsets = synth.batch_rids(n, n, kind, 5)
+    rows = int(n.max())
+    tables = {r: synth.records(rows, r, 100 + r) for r in synth.BATCH_RECS}
+    d_tab = {r: to_dev(t) for r, t in tables.items()}
+    waves, cur, cur_bytes = [], [], 0
+    for k in range(n.size):
+        b = int(n[k]) * int(rec[k])
+        if cur and cur_bytes + b > 48e9:
+            waves.append(cur)
+            cur, cur_bytes = [], 0
+        cur.append(k)
+        cur_bytes += b
+    waves.append(cur)
+    cores = os.cpu_count() or 1
+    checked = 0
+    for wave in waves:
+        reqs, slices = [], []
+        for r in synth.BATCH_RECS:
+            ks = [k for k in wave if int(rec[k]) == r]
+            if not ks:
+                continue
+            cat = np.concatenate([all_rids[int(offsets[k]):int(offsets[k]) + int(n[k])] for k in ks])
+            d_rids = to_dev(cat)
+            arena = torch.empty((cat.size, r), dtype=torch.uint8, device=DEV)
+            at = 0
+            for k in ks:
+                m = int(n[k])
+                reqs.append((d_tab[r], m, d_rids[at:at + m], arena[at:at + m]))
+                slices.append((k, r, arena[at:at + m]))
+                at += m
+        ctx.retrieve_batch(reqs)
+        ctx.sync()
+        for k, r, out in slices:
+            m = int(n[k])
+            want = oracle.retrieve_threads(tables[r][:m], all_rids[int(offsets[k]):int(offsets[k]) + m], cores)
+            assert_rows_equal(out, want, f"batch request {k} ({m} x {r} B)")
+            checked += 1
+        del reqs, slices, arena, d_rids
+        torch.cuda.empty_cache()
+    assert checked == 4096

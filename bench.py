@@ -52,6 +52,8 @@ def args_():
     p.add_argument("--e2e-lanes", type=int, default=3,
                    help="contexts (each on its own host thread and stream) taking alternate end-to-end steps")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-tune", action="store_true",
+                   help="time the plan chosen by record size (or DPG_VARIANT) instead of the dpg_tune winner")
     p.add_argument("--no-small", action="store_true",
                    help="skip the 16-byte-record point (62,500,000 records, permutation rids) of the line")
     p.add_argument("--sweep-recs", default="16,32,64,100,256", help="record sizes of --sweep")
@@ -720,7 +722,12 @@ def main():
     del g_pairs
 
     # pick the DPG plan for this shape by timing the candidates (outside the timed region)
-    plan = ctx.tune(d_src, d_pairs, d_out, rid_stride=16, rid_off=12)
+    if a.no_tune:
+        ctx.sort_copy(d_pairs, d_src, out=d_out)
+        ctx.sync()
+        plan = ctx.last_plan()
+    else:
+        plan = ctx.tune(d_src, d_pairs, d_out, rid_stride=16, rid_off=12)
 
     ms_dpg, launches, win = timed(lambda: ctx.sort_copy(d_pairs, d_src, out=d_out))
     ms_dir, launches_dir, win_dir = timed(lambda: ctx.sort_copy_direct(d_pairs, d_src, out=d_out))
@@ -866,7 +873,8 @@ def main():
                        "algorithmic_bytes_per_step": alg_bytes,
                        "l2": "inputs larger than L2 (2.16 GB read/written per step vs 126 MB L2); no flush",
                        "plan": {"variant": plan[0], "seg_log2": plan[1],
-                                "picked_by": "dpg_tune (CUDA-event timing of the candidate plans)"},
+                                "picked_by": "record-size default" if a.no_tune else
+                                "dpg_tune (CUDA-event timing of the candidate plans)"},
                        "parallelism": f"replicas x{world}"},
             "pct_of_hbm_peak": round(value / world / peak, 4),
             "records_per_s": round(world * n / (ms_dpg * 1e-3), 1),

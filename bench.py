@@ -90,17 +90,17 @@ def args_():
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one
 # ncu capture of the headline workload (n = 10,000,000, rec = 100), keyed by
-# plan variant and kernel (L2-run plan captured with 65,536-record runs, the
-# 3-pass plan with 512-record segments; the run length does not change what
-# these kernels read and write); valid only while the retrieval sources hash
-# to `src_sha256` (any edit of them nulls the figure).
+# plan variant and kernel (L2-run plan captured with 131,072-record runs, the
+# tuner's pick; the 3-pass plan with 512-record segments; the run length does
+# not change what these kernels read and write); valid only while the
+# retrieval sources hash to `src_sha256` (any edit of them nulls the figure).
 NCU_TRAFFIC = {
-    "src_sha256": "6f6c77536833accbe0314011a52a87e6d9bde62178d7e1702c0e74d2be84dbd4"
-                  ":ea4aa05df714562de946e6caba3cc9da73b7638cf8349e76339692c3d9d2f8e6"
-                  ":3855e8849060e1679f0ff4c0a4d780ef201c67030b4327071279271201401681",
+    "src_sha256": "e981d57d2792ccc319f2eef4bd96698f7e60501411f3c26dafbe997c62a7e3f6"
+                  ":5bb7b838d052edacf49967a9b75593f80b9c80aff4fea6f1b12487c539627886"
+                  ":6a8eaedc414081fb2429ddcea50cd0f628d9e7c91ff0c6ed0a55dcd1e3c92b27",
     "n": 10_000_000, "rec": 100,
-    "bytes": {"4/k_probe_l2": 1040257792 + 959681024, "4/k_gather_phase3": 1060956416 + 955388416,
-              "3/k_probe": 1020185856 + 943697664, "3/k_gather_phase3": 1040556032 + 955550976},
+    "bytes": {"4/k_probe_l2": 1040092928 + 959998464, "4/k_gather_phase3": 1051905536 + 954563840,
+              "3/k_probe": 1020206336 + 945263104, "3/k_gather_phase3": 1040539392 + 955459840},
 }
 
 TRAFFIC_SOURCES = ("dpg_retrieve.cu", "dpg_runs.cu", "dpg_device.cuh")
@@ -567,6 +567,9 @@ def serve_one(a, rate, dev, R, recs, tables, perm, d_dim, d_fact, t_setup):
             last_done = time.perf_counter()
             if k in sample and out is not None:
                 kept[k] = out.clone()
+                # the copy runs on torch's stream: it must finish before the
+                # server may hand the memory to another job
+                torch.cuda.current_stream(dev).synchronize()
             srv.release(pending.pop(k))
             if block:
                 return

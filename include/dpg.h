@@ -259,7 +259,10 @@ dpg_status dpg_server_submit(dpg_server* srv, const dpg_job* job, uint64_t* tick
  * wait == 0 returns DPG_EBUSY while the job is pending. */
 dpg_status dpg_server_result(dpg_server* srv, uint64_t ticket, int wait, void** result, size_t* result_bytes,
                              double* latency_ms);
-/* Free a completed job's result and forget the ticket. */
+/* Free a completed job's result and forget the ticket.  The memory returns
+ * to the server's pool in the order of the job's stream and may be handed to
+ * the next job at once: work the caller enqueued on its own streams that
+ * reads the result must have finished before this call. */
 dpg_status dpg_server_release(dpg_server* srv, uint64_t ticket);
 /* Device bytes currently held by running jobs and unreleased results. */
 size_t dpg_server_held_bytes(dpg_server* srv);

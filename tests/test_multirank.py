@@ -49,3 +49,33 @@ def test_single_process_aggregation():
     import bench
     assert bench.max_over_ranks(None, 2.5, "cpu") == 2.5
     assert bench.job_gbs(1, 1_000_000_000, 1.0) == pytest.approx(1000.0)
+
+
+def _failing_worker(rank, world, port, out):
+    import datetime
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    import bench
+    try:
+        if rank == 1:
+            raise RuntimeError("rank 1 fails before its step is aggregated")
+        bench.max_over_ranks(dist, 1.0, "cpu")   # waits for rank 1, which never joins
+        out[rank] = "completed"
+    except RuntimeError as e:
+        out[rank] = f"error: {type(e).__name__}"
+    finally:
+        if rank == 0:
+            dist.destroy_process_group()
+
+
+def test_a_failing_rank_ends_the_others_with_an_error_gloo():
+    """A rank that raises before the cross-rank aggregation: the surviving
+    rank's collective ends with an error once the process-group timeout
+    passes, instead of waiting for ever."""
+    world, port = 2, 29533
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_failing_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[1].startswith("error")
+    assert res[0].startswith("error")

@@ -12,12 +12,18 @@
 // (k_extract_pairs here, the join's k_extract_fk_pairs): the counts do not
 // depend on the order.  Each pass is then one kernel, k_rs_onesweep: a CTA
 // takes the next tile (64 KB of pairs), ranks its pairs stably (per-warp
-// digit counts, the lanes sharing a digit found with a shared-memory OR, a
-// prefix over warps), publishes the tile's digit counts, finds how many pairs
-// of each digit earlier tiles hold by looking back over their published
-// counts (decoupled look-back; every wait is bounded), then reorders the tile
-// in shared memory and writes each digit's pairs as one contiguous piece at
-// digit base + earlier tiles' count.
+// digit counts; the lanes sharing a digit are the AND of eight ballots, one
+// per digit bit), publishes the tile's digit counts, finds how many pairs of
+// each digit earlier tiles hold by looking back over their published counts
+// (decoupled look-back; every wait is bounded) while the other half of the
+// CTA lays the tile out, then reorders the tile in shared memory and writes
+// each digit's pairs as one contiguous piece at digit base + earlier tiles'
+// count.
+//
+// dpg_sort_keyptr sorts 16-byte key-pointer pairs.  dpg_sort_records needs
+// only the order of the rids, so it sorts 8-byte (key word, rid) pairs: the
+// key in 4-byte groups from its least significant end, the pass that starts
+// a group swapping that group's word in from a per-rid side array.
 #include <algorithm>
 
 #include "dpg_device.cuh"
@@ -34,6 +40,10 @@ constexpr int kRsThreads = 512;
 constexpr int kRsMinBlocks = 2;
 constexpr int kRsWarps = kRsThreads / 32;
 template <class E> __host__ __device__ constexpr int rs_items() { return sizeof(E) == 16 ? 8 : 16; }
+// earlier tiles read per step of the look-back: 8 for 16-byte pairs (3 us
+// less per pass over 1e7 pairs than 1); 1 for 8-byte pairs, whose 16 pairs
+// per thread leave no registers for a window
+template <class E> __host__ __device__ constexpr int rs_look_win() { return sizeof(E) == 16 ? 8 : 1; }
 // pairs per tile
 template <class E> __host__ __device__ constexpr uint32_t rs_tile() { return kRsThreads * rs_items<E>(); }
 
@@ -75,6 +85,57 @@ __global__ void __launch_bounds__(256)
     if (h[x]) atomicAdd(&counts[x], h[x]);
 }
 
+// Phase 1 for the 8-byte sort: the key of record i in groups of 4 bytes
+// from its least significant end (group g = bytes [K - 4g - 4, K - 4g),
+// clipped at 0; byte j at bits 8 * (j % 4) of its group's word).  pairs[i] =
+// (group 0's word, i), side1/side2[i] = group 1's and group 2's words (the
+// passes that start those groups read them; null when the key has no such
+// group), and the digit counts of every key byte (counts[j * 256 + d], zero
+// on entry).
+template <bool WORDS>
+__global__ void __launch_bounds__(256)
+    k_extract_pairs8(const uint8_t* __restrict__ src, uint64_t n, uint32_t rec, uint32_t key_bytes,
+                     uint2* __restrict__ pairs, uint32_t* __restrict__ side1, uint32_t* __restrict__ side2,
+                     uint32_t* __restrict__ counts) {
+  __shared__ uint32_t h[12 * 256];
+  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x) h[x] = 0;
+  __syncthreads();
+  const uint32_t nw = (key_bytes + 3) / 4;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint8_t* r = src + i * rec;
+    uint32_t w[3] = {0u, 0u, 0u};
+    if (WORDS) {
+      const uint32_t* rw = reinterpret_cast<const uint32_t*>(r);
+#pragma unroll
+      for (uint32_t j = 0; j < 3; ++j)
+        if (j < nw) {
+          const uint32_t keep = key_bytes >= 4 * (j + 1) ? 32u : 8u * (key_bytes - 4 * j);
+          const uint32_t v = __ldg(rw + j);
+          w[j] = keep == 32u ? v : (v & ((1u << keep) - 1u));
+        }
+    } else {
+#pragma unroll
+      for (uint32_t b = 0; b < 12; ++b)
+        if (b < key_bytes) w[b >> 2] |= (uint32_t)__ldg(r + b) << (8 * (b & 3));
+    }
+    // group g holds bytes [lo, hi): the bytes of words lo/4 .. (hi-1)/4 in range
+    uint32_t gw[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (uint32_t g = 0; g < 3; ++g) {
+      const int hi = (int)key_bytes - 4 * (int)g, lo = hi - 4 < 0 ? 0 : hi - 4;
+      if (hi <= 0) break;
+      for (int j = lo; j < hi; ++j) gw[g] |= w[j >> 2] & (0xffu << (8 * (j & 3)));
+    }
+    pairs[i] = make_uint2(gw[0], (uint32_t)i);
+    if (side1) side1[i] = gw[1];
+    if (side2) side2[i] = gw[2];
+    for (uint32_t j = 0; j < key_bytes; ++j) atomicAdd(&h[j * 256 + ((w[j >> 2] >> (8 * (j & 3))) & 0xffu)], 1u);
+  }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x)
+    if (h[x]) atomicAdd(&counts[x], h[x]);
+}
+
 // Key byte `byte` of a pair: 16-byte pairs hold up to 12 key bytes in words
 // x, y, z; 8-byte pairs (the DPG-sort join's) up to 4 in x, the rid in y.
 __device__ __forceinline__ uint32_t pair_digit(const uint4& p, uint32_t byte) {
@@ -89,28 +150,30 @@ constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kCountMask = (1u
 
 // One stable pass on key byte `byte`.  Tiles are numbered in the order CTAs
 // start (tile_ctr), so a tile only waits for tiles whose CTAs already run.
-// E: uint4 (16-byte pairs) or uint2 (8-byte pairs).
-template <class E>
+// E: uint4 (16-byte pairs) or uint2 (8-byte pairs).  SWAP (8-byte pairs):
+// the pass starts a new key group, so each pair's key word is first replaced
+// by gword[rid] (that group's word).
+template <class E, bool SWAP = false>
 __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
     k_rs_onesweep(const E* __restrict__ in, E* __restrict__ out, uint64_t n, uint32_t byte,
                   const uint32_t* __restrict__ digit_count, uint32_t* status, uint32_t* tile_ctr, int* err,
-                  long long wait_limit) {
-  __shared__ uint16_t whist[kRsWarps][256];
-  __shared__ uint32_t wmask[kRsWarps][256];  // lanes of a warp holding digit d in this round
-  __shared__ uint32_t tcnt[256], toff[256], s_base[256], s_excl[256];
+                  long long wait_limit, const uint32_t* __restrict__ gword = nullptr) {
+  __shared__ uint16_t whist[kRsWarps][256];  // pairs of digit d in warp w's share of the tile
+  __shared__ uint16_t wslot[kRsWarps][256];  // tile slot of warp w's first pair of digit d
+  __shared__ uint32_t s_base[256];           // output position of the pass's first pair of digit d
+  __shared__ uint32_t s_gpos[256];           // output position of this tile's first pair of digit d
+  __shared__ uint32_t s_toff[256];           // tile slot of this tile's first pair of digit d
+  __shared__ uint32_t s_wsum[8];
   __shared__ uint32_t s_tile;
   constexpr int kItems = rs_items<E>();
   constexpr uint32_t kTile = rs_tile<E>();
+  static_assert(kTile <= 65536, "tile slots are 16-bit");
   extern __shared__ uint4 sraw[];
-  E* sbuf = reinterpret_cast<E*>(sraw);                      // kTile pairs
-  uint8_t* sdig = reinterpret_cast<uint8_t*>(sbuf + kTile);  // kTile digits
+  E* sbuf = reinterpret_cast<E*>(sraw);  // kTile pairs
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
-  for (uint32_t x = threadIdx.x; x < kRsWarps * 256; x += kRsThreads) {
-    (&whist[0][0])[x] = 0;
-    (&wmask[0][0])[x] = 0;
-  }
+  for (uint32_t x = threadIdx.x; x < kRsWarps * 128; x += kRsThreads) reinterpret_cast<uint32_t*>(&whist[0][0])[x] = 0;
   __syncthreads();
   const uint32_t t = s_tile;
   const uint64_t base = (uint64_t)t * kTile;
@@ -138,101 +201,117 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
   // this thread's pairs: kItems rounds of 32 consecutive pairs of its warp
   // (the digit is recomputed from the pair where it is needed)
   const uint64_t e0 = base + (uint64_t)warp * (32 * kItems) + lane;
+  const uint32_t rem = n > e0 ? (n - e0 < kTile ? (uint32_t)(n - e0) : kTile) : 0u;  // item k valid: 32k < rem
+  const E* __restrict__ inp = in + e0;
   E v[kItems];
-  uint32_t rank[kItems];
+  uint32_t rank2[kItems / 2];  // two 16-bit in-warp ranks per word (a rank is below the tile size)
   // all of the tile's loads first: the ranking below has warp barriers,
   // which would otherwise hold each load back until the previous round ends
 #pragma unroll
   for (int k = 0; k < kItems; ++k)
-    if (e0 + (uint64_t)k * 32 < n) v[k] = in[e0 + (uint64_t)k * 32];
+    if ((uint32_t)k * 32 < rem) v[k] = inp[k * 32];
+  if constexpr (SWAP) {
+#pragma unroll
+    for (int k = 0; k < kItems; ++k)
+      if ((uint32_t)k * 32 < rem) v[k].x = gword[v[k].y];
+  }
+  // stable in-warp ranks: round k's peers (valid lanes with the same digit)
+  // are the AND of eight ballots, one per digit bit; the lane's rank is the
+  // warp's count of that digit in earlier rounds plus its peers below it
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
-    const bool ok = e0 + (uint64_t)k * 32 < n;
+    const bool ok = (uint32_t)k * 32 < rem;
     const uint32_t d = ok ? pair_digit(v[k], byte) : 0u;
-    // peers: the lanes of this warp with the same digit, gathered by a
-    // shared-memory OR (cheaper here than __match_any_sync)
-    if (ok) atomicOr(&wmask[warp][d], 1u << lane);
-    __syncwarp();
-    const uint32_t peers = ok ? wmask[warp][d] : (1u << lane);
-    const uint32_t before = __popc(peers & lt);
-    uint32_t prior = 0;
-    if (ok) prior = whist[warp][d];
-    __syncwarp();
-    if (ok && before == 0) {
-      whist[warp][d] = (uint16_t)(prior + __popc(peers));
-      wmask[warp][d] = 0;
+    uint32_t peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const uint32_t bit = (d >> b) & 1u;
+      peers &= __ballot_sync(0xffffffffu, bit != 0u) ^ (bit - 1u);
     }
+    const uint32_t before = __popc(peers & lt);
+    const uint32_t prior = ok ? whist[warp][d] : 0u;
     __syncwarp();
-    rank[k] = prior + before;
+    if (ok && before == 0) whist[warp][d] = (uint16_t)(prior + __popc(peers));
+    __syncwarp();
+    if (k & 1) rank2[k >> 1] |= (prior + before) << 16;
+    else rank2[k >> 1] = prior + before;
   }
   __syncthreads();
-  if (threadIdx.x < 256) {  // exclusive prefix over warps, per digit
-    uint32_t run = 0;
-    for (int w = 0; w < kRsWarps; ++w) {
-      const uint32_t c = whist[w][threadIdx.x];
-      whist[w][threadIdx.x] = (uint16_t)run;
-      run += c;
-    }
-    tcnt[threadIdx.x] = run;
-    // publish this tile's count of digit d, then look back over earlier tiles
+  const uint32_t dg = threadIdx.x & 255;
+  uint32_t cnt = 0;  // the tile's count of digit dg
+#pragma unroll
+  for (int w = 0; w < kRsWarps; ++w) cnt += whist[w][dg];
+  if (threadIdx.x < 256) {
+    // publish this tile's count of digit dg, then look back over earlier tiles
     volatile uint32_t* st = status;
-    const uint32_t dg = threadIdx.x;
-    st[(uint64_t)t * 256 + dg] = (t == 0 ? kFlagPrefix : kFlagAgg) | run;
+    st[(uint64_t)t * 256 + dg] = (t == 0 ? kFlagPrefix : kFlagAgg) | cnt;
     uint32_t excl = 0;
     if (t > 0) {
       // tile j < t was claimed before this one, so its CTA is running and
-      // publishes its count; the wait is bounded all the same
-      for (int64_t j = (int64_t)t - 1; j >= 0; --j) {
-        bool ok;
-        const uint32_t w = wait_word_bounded(status + (uint64_t)j * 256 + dg, wait_limit, &ok,
-                                             [](uint32_t x) { return (x & ~kCountMask) != 0; });
-        if (!ok) {
-          atomicOr(err, ERR_TIMEOUT);
-          break;
-        }
-        excl += w & kCountMask;
-        if ((w & ~kCountMask) == kFlagPrefix) break;
-      }
-      st[(uint64_t)t * 256 + dg] = kFlagPrefix | (excl + run);
-    }
-    s_excl[dg] = excl;
-  }
-  __syncthreads();
-  if (warp == 0) {  // exclusive scan of the tile's 256 digit counts, 8 per lane
-    uint32_t c[8], sum = 0;
+      // publishes its count; the wait is bounded all the same.  The walk
+      // reads kLookWin earlier tiles at a time (independent loads), then
+      // sums them from the nearest down to the first inclusive prefix.
+      constexpr int kLookWin = rs_look_win<E>();
+      bool fin = false;
+      for (int64_t j = (int64_t)t - 1; !fin && j >= 0; j -= kLookWin) {
+        uint32_t w[kLookWin];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      c[j] = tcnt[lane * 8 + j];
-      sum += c[j];
+        for (int i = 0; i < kLookWin; ++i) w[i] = j - i >= 0 ? st[(uint64_t)(j - i) * 256 + dg] : 0u;
+#pragma unroll
+        for (int i = 0; i < kLookWin; ++i) {
+          if (!fin && j - i >= 0) {
+            uint32_t x = w[i];
+            bool ok = true;
+            if ((x & ~kCountMask) == 0)
+              x = wait_word_bounded(status + (uint64_t)(j - i) * 256 + dg, wait_limit, &ok,
+                                    [](uint32_t y) { return (y & ~kCountMask) != 0; });
+            if (!ok) {
+              atomicOr(err, ERR_TIMEOUT);
+              fin = true;
+            } else {
+              excl += x & kCountMask;
+              fin = (x & ~kCountMask) == kFlagPrefix;
+            }
+          }
+        }
+      }
+      st[(uint64_t)t * 256 + dg] = kFlagPrefix | (excl + cnt);
     }
-    uint32_t x = sum;
+    s_gpos[dg] = s_base[dg] + excl;
+  } else {
+    // meanwhile the upper 256 threads lay out the tile: exclusive scan of the
+    // counts over digits, then each warp's first slot per digit
+    uint32_t x = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    uint32_t run = x - sum;
+    if (lane == 31) s_wsum[warp - 8] = x;
+    asm volatile("bar.sync 1, 256;" ::: "memory");
+    uint32_t off = x - cnt;
+    for (int w = 0; w < warp - 8; ++w) off += s_wsum[w];
+    s_toff[dg] = off;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      toff[lane * 8 + j] = run;
-      run += c[j];
+    for (int w = 0; w < kRsWarps; ++w) {
+      wslot[w][dg] = (uint16_t)off;
+      off += whist[w][dg];
     }
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kItems; ++k) {
-    if (e0 + (uint64_t)k * 32 < n) {
+    if ((uint32_t)k * 32 < rem) {
       const uint32_t d = pair_digit(v[k], byte);
-      const uint32_t p = toff[d] + whist[warp][d] + rank[k];
-      sbuf[p] = v[k];
-      sdig[p] = (uint8_t)d;
+      sbuf[wslot[warp][d] + ((rank2[k >> 1] >> (16 * (k & 1))) & 0xffffu)] = v[k];
     }
   }
   __syncthreads();
   const uint32_t tn = (uint32_t)((n - base) < kTile ? (n - base) : kTile);
   for (uint32_t p = threadIdx.x; p < tn; p += kRsThreads) {
-    const uint32_t dg = sdig[p];
-    out[(uint64_t)s_base[dg] + s_excl[dg] + (p - toff[dg])] = sbuf[p];
+    const E q = sbuf[p];
+    const uint32_t d = pair_digit(q, byte);
+    out[(uint64_t)(uint32_t)(s_gpos[d] + (p - s_toff[d]))] = q;
   }
 }
 
@@ -265,7 +344,7 @@ uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint
   uint32_t* tile_ctr = radix_counts(scan) + 12 * 256;
   uint32_t* tile_status = reinterpret_cast<uint32_t*>(scan + 16384);
   cudaError_t e = cudaSuccess;
-  const size_t smem = rs_tile<E>() * (sizeof(E) + 1);
+  const size_t smem = rs_tile<E>() * sizeof(E);
   cudaFuncSetAttribute(k_rs_onesweep<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (int byte = (int)key_bytes - 1; byte >= 0; --byte) {
     e = cudaMemsetAsync(tile_status, 0, (size_t)ntiles * 256 * 4, st);
@@ -290,6 +369,79 @@ uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint
 }  // namespace
 
 uint32_t* radix_counts(uint8_t* scan) { return reinterpret_cast<uint32_t*>(scan); }
+
+size_t sort_pairs8_tmp_bytes(uint64_t n, uint32_t key_bytes) {
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const uint32_t groups = (key_bytes + 3) / 4;
+  return 2 * al(n * 8) + (groups > 1 ? groups - 1 : 0) * al(n * 4);
+}
+
+namespace {
+
+template <bool SWAP>
+void rs_pass8(dpg_ctx& ctx, const uint2* in, uint2* out, uint64_t n, uint32_t byte, const uint32_t* counts,
+              uint32_t* status, uint32_t* tile_ctr, const uint32_t* gword, cudaStream_t st) {
+  const uint32_t ntiles = (uint32_t)((n + rs_tile<uint2>() - 1) / rs_tile<uint2>());
+  const size_t smem = rs_tile<uint2>() * sizeof(uint2);
+  auto kern = k_rs_onesweep<uint2, SWAP>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  TraceScope ts(ctx, SWAP ? "k_rs_onesweep8_swap" : "k_rs_onesweep8", st);
+  kern<<<ntiles, kRsThreads, smem, st>>>(in, out, n, byte, counts + 256 * byte, status, tile_ctr, ctx.d_err,
+                                         ctx.wait_cycles, gword);
+  ctx.launches++;
+}
+
+}  // namespace
+
+// Phases 1 and 2 of §3 on 8-byte pairs (the rid order only): the LSD passes
+// run over (group word, rid) pairs, group 0 being the key's 4 least
+// significant bytes; the first pass of group g >= 1 swaps in side[g][rid]
+// (stability keeps the order the bytes already sorted gave, and no later
+// pass needs those bytes again).  *final8 = the sorted pairs (rid at byte 4)
+// inside tmp (sort_pairs8_tmp_bytes).
+int run_sort_pairs8(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, uint32_t key_bytes, uint8_t* tmp,
+                    uint8_t* scan, cudaStream_t st, uint8_t** final8) {
+  if (key_bytes == 0 || key_bytes > 12 || n > kCountMask) return DPG_EINVAL;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  uint2* buf[2] = {reinterpret_cast<uint2*>(tmp), reinterpret_cast<uint2*>(tmp + al(n * 8))};
+  *final8 = tmp;
+  if (n == 0) return DPG_OK;
+  const uint32_t groups = (key_bytes + 3) / 4;
+  uint32_t* side[3] = {nullptr, nullptr, nullptr};
+  for (uint32_t g = 1; g < groups; ++g)
+    side[g] = reinterpret_cast<uint32_t*>(tmp + 2 * al(n * 8) + (g - 1) * al(n * 4));
+  uint32_t* counts = radix_counts(scan);
+  uint32_t* tile_ctr = counts + 12 * 256;
+  uint32_t* tile_status = reinterpret_cast<uint32_t*>(scan + 16384);
+  cudaError_t e = cudaMemsetAsync(counts, 0, 12 * 256 * 4, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  {
+    TraceScope ts(ctx, "k_extract_pairs", st);
+    const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx.sms * 8);
+    if (rec % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 4 == 0)
+      k_extract_pairs8<true><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, buf[0], side[1], side[2], counts);
+    else
+      k_extract_pairs8<false><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, buf[0], side[1], side[2], counts);
+    ctx.launches++;
+  }
+  int cur = 0;
+  for (int byte = (int)key_bytes - 1; byte >= 0; --byte) {
+    const uint32_t from_end = (uint32_t)((int)key_bytes - 1 - byte);
+    const uint32_t g = from_end / 4;
+    const uint32_t ntiles = (uint32_t)((n + rs_tile<uint2>() - 1) / rs_tile<uint2>());
+    e = cudaMemsetAsync(tile_status, 0, (size_t)ntiles * 256 * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+    if (g > 0 && from_end % 4 == 0)
+      rs_pass8<true>(ctx, buf[cur], buf[cur ^ 1], n, (uint32_t)byte, counts, tile_status, tile_ctr, side[g], st);
+    else
+      rs_pass8<false>(ctx, buf[cur], buf[cur ^ 1], n, (uint32_t)byte, counts, tile_status, tile_ctr, nullptr, st);
+    cur ^= 1;
+  }
+  *final8 = reinterpret_cast<uint8_t*>(buf[cur]);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "sort launch");
+}
 
 uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
                          cudaStream_t st, int* status) {

@@ -35,8 +35,11 @@ def tie_heavy(n, rec, seed):
     return src
 
 
-@pytest.mark.parametrize("n", [1, 2, 100, 4095, 4096, 4097, 100_003])
-@pytest.mark.parametrize("rec,key_bytes", [(10, 10), (16, 10), (100, 10), (13, 3), (12, 12), (256, 1), (100, 7)])
+# n spans the 8192-pair tile of the radix passes (one, several and ragged);
+# key lengths put 1, 2 and 3 four-byte key groups with every tail length
+@pytest.mark.parametrize("n", [1, 2, 100, 4095, 4097, 8191, 8192, 8193, 24_581, 100_003])
+@pytest.mark.parametrize("rec,key_bytes", [(10, 10), (16, 10), (100, 10), (13, 3), (12, 12), (256, 1), (100, 7),
+                                           (8, 4), (12, 5), (20, 8), (9, 9), (11, 11)])
 def test_sort_keyptr_matches_oracle(ctx, n, rec, key_bytes):
     for src in (synth.records(n, rec, n + rec), tie_heavy(n, rec, 5)):
         want = oracle.sort_keyptr(src, key_bytes)

@@ -332,7 +332,7 @@ dpg_status dpg_sort_keyptr(dpg_ctx* c, const void* src, size_t n_src, size_t rec
   if (s != DPG_OK || n_src == 0) return (dpg_status)s;
   if (overlaps(src, n_src * rec, pairs, n_src * 16)) return DPG_EINVAL;
   DeviceGuard g(c->device);
-  const size_t bt = al256(n_src * 16), bs = dpg::sort_scan_bytes(n_src);
+  const size_t bt = al256(dpg::sort_keyptr_tmp_bytes(n_src, (uint32_t)key_bytes)), bs = dpg::sort_scan_bytes(n_src);
   if ((s = dpg::ensure_aux(*c, bt + bs))) return (dpg_status)s;
   uint8_t* tmp = static_cast<uint8_t*>(c->aux);
   return (dpg_status)dpg::run_sort_keyptr(*c, static_cast<const uint8_t*>(src), n_src, (uint32_t)rec,

@@ -50,14 +50,15 @@ template <class E> __host__ __device__ constexpr uint32_t rs_tile() { return kRs
 // Phase 1: pairs[i] = (key of record i, zero pad, i).  WORDS: records and
 // the table are 4-byte aligned, so the key is read as ceil(key_bytes/4)
 // words (never past the record: key_bytes <= rec, rec a multiple of 4).
-// The digit counts of every key byte (counts[j * 256 + d], zero on entry)
-// are taken on the way, so the radix sort need not read the pairs for them.
+// The digit counts of the first count_bytes key bytes (counts[j * 256 + d],
+// zero on entry) are taken on the way, so the radix passes need not read the
+// pairs for them.
 template <bool WORDS>
 __global__ void __launch_bounds__(256)
     k_extract_pairs(const uint8_t* __restrict__ src, uint64_t n, uint32_t rec, uint32_t key_bytes,
-                    uint4* __restrict__ pairs, uint32_t* __restrict__ counts) {
+                    uint32_t count_bytes, uint4* __restrict__ pairs, uint32_t* __restrict__ counts) {
   __shared__ uint32_t h[12 * 256];
-  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x) h[x] = 0;
+  for (uint32_t x = threadIdx.x; x < count_bytes * 256; x += blockDim.x) h[x] = 0;
   __syncthreads();
   const uint32_t nw = (key_bytes + 3) / 4;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -78,10 +79,10 @@ __global__ void __launch_bounds__(256)
         if (b < key_bytes) w[b >> 2] |= (uint32_t)__ldg(r + b) << (8 * (b & 3));
     }
     pairs[i] = make_uint4(w[0], w[1], w[2], w[3]);
-    for (uint32_t j = 0; j < key_bytes; ++j) atomicAdd(&h[j * 256 + ((w[j >> 2] >> (8 * (j & 3))) & 0xffu)], 1u);
+    for (uint32_t j = 0; j < count_bytes; ++j) atomicAdd(&h[j * 256 + ((w[j >> 2] >> (8 * (j & 3))) & 0xffu)], 1u);
   }
   __syncthreads();
-  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x)
+  for (uint32_t x = threadIdx.x; x < count_bytes * 256; x += blockDim.x)
     if (h[x]) atomicAdd(&counts[x], h[x]);
 }
 
@@ -149,15 +150,19 @@ __device__ __forceinline__ uint32_t pair_digit(const uint2& p, uint32_t byte) {
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kCountMask = (1u << 30) - 1;
 
 // One stable pass on key byte `byte`.  Tiles are numbered in the order CTAs
-// start (tile_ctr), so a tile only waits for tiles whose CTAs already run.
-// E: uint4 (16-byte pairs) or uint2 (8-byte pairs).  SWAP (8-byte pairs):
-// the pass starts a new key group, so each pair's key word is first replaced
-// by gword[rid] (that group's word).
-template <class E, bool SWAP = false>
+// claim them (tile_ctr), so a tile only waits for tiles whose CTAs already
+// run.  E: uint4 (16-byte pairs) or uint2 (8-byte pairs).  SWAP (8-byte
+// pairs): the pass starts a new key group, so each pair's key word is first
+// replaced by gword[rid] (that group's word).  DEVN: the pair count is
+// *n_dev (known only on the device) and each CTA claims tiles until none is
+// left; a CTA finishes a tile before it claims the next, so the waits stay
+// on tiles of running CTAs.
+template <class E, bool SWAP = false, bool DEVN = false>
 __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
-    k_rs_onesweep(const E* __restrict__ in, E* __restrict__ out, uint64_t n, uint32_t byte,
+    k_rs_onesweep(const E* __restrict__ in, E* __restrict__ out, uint64_t n_arg, uint32_t byte,
                   const uint32_t* __restrict__ digit_count, uint32_t* status, uint32_t* tile_ctr, int* err,
-                  long long wait_limit, const uint32_t* __restrict__ gword = nullptr) {
+                  long long wait_limit, const uint32_t* __restrict__ gword = nullptr,
+                  const uint32_t* __restrict__ n_dev = nullptr) {
   __shared__ uint16_t whist[kRsWarps][256];  // pairs of digit d in warp w's share of the tile
   __shared__ uint16_t wslot[kRsWarps][256];  // tile slot of warp w's first pair of digit d
   __shared__ uint32_t s_base[256];           // output position of the pass's first pair of digit d
@@ -172,10 +177,14 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
   E* sbuf = reinterpret_cast<E*>(sraw);  // kTile pairs
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
+  const uint64_t n = DEVN ? (uint64_t)*n_dev : n_arg;
+  const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
+  for (;;) {
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
   for (uint32_t x = threadIdx.x; x < kRsWarps * 128; x += kRsThreads) reinterpret_cast<uint32_t*>(&whist[0][0])[x] = 0;
   __syncthreads();
   const uint32_t t = s_tile;
+  if (DEVN && t >= ntiles) break;
   const uint64_t base = (uint64_t)t * kTile;
   // digit bases of this pass: exclusive scan of the digit counts (warp 1, 8 per lane)
   if (warp == 1) {
@@ -313,6 +322,175 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
     const uint32_t d = pair_digit(q, byte);
     out[(uint64_t)(uint32_t)(s_gpos[d] + (p - s_toff[d]))] = q;
   }
+  if (!DEVN) break;
+  __syncthreads();  // the next tile reuses shared memory
+  }
+}
+
+// ---- the bucket stage: after two LSD passes on key bytes 1 and 0 the pairs
+// lie in 65,536 buckets of equal two-byte prefix, each in rid order; every
+// bucket is then sorted on the rest of its key.
+
+constexpr uint32_t kBuckets = 65536;
+constexpr uint32_t kBucketMax = 256;  // the largest bucket a warp sorts itself
+constexpr int kBsWarps = 8;
+
+__device__ __forceinline__ uint32_t pair_prefix(const uint4& p) { return ((p.x & 0xffu) << 8) | ((p.x >> 8) & 0xffu); }
+
+// off[b] = position of the first pair with prefix >= b (off[kBuckets] = n):
+// each position i writes the buckets strictly after its predecessor's prefix
+// up to its own (position n: up to kBuckets).
+__global__ void __launch_bounds__(256) k_bucket_bounds(const uint4* __restrict__ pairs, uint64_t n,
+                                                       uint32_t* __restrict__ off) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = i < n ? pair_prefix(pairs[i]) : kBuckets;
+    const int64_t q = i > 0 ? (int64_t)pair_prefix(pairs[i - 1]) : -1;
+    for (int64_t b = q + 1; b <= (int64_t)p; ++b) off[b] = (uint32_t)i;
+  }
+}
+
+// Key bytes 3.. of a pair as big-endian words, then the rid: the order
+// inside a run of equal first three key bytes.
+__device__ __forceinline__ bool tail_greater(const uint4& a, const uint4& b) {
+  const uint32_t a0 = __byte_perm(a.x, a.y, 0x3456), b0 = __byte_perm(b.x, b.y, 0x3456);
+  if (a0 != b0) return a0 > b0;
+  const uint32_t a1 = __byte_perm(a.y, a.z, 0x3456), b1 = __byte_perm(b.y, b.z, 0x3456);
+  if (a1 != b1) return a1 > b1;
+  if ((a.z >> 24) != (b.z >> 24)) return (a.z >> 24) > (b.z >> 24);
+  return a.w > b.w;
+}
+
+constexpr uint32_t kRunMax = 32;  // the longest run of equal key byte 2 a lane sorts by insertion
+
+// Each warp sorts whole buckets of up to kBucketMax pairs in place: a
+// counting sort on key byte 2 in shared memory (the scatter order inside a
+// digit does not matter), then each run of equal byte 2 sorted by insertion
+// on the rest of the key and the rid, one lane per run.  A bucket larger
+// than kBucketMax, or with a run longer than kRunMax, is appended whole (in
+// its rid order) to big[] for the LSD fallback.
+__global__ void __launch_bounds__(kBsWarps * 32) k_bucket_sort(uint4* __restrict__ pairs,
+                                                               const uint32_t* __restrict__ off,
+                                                               uint4* __restrict__ big, uint32_t* __restrict__ nbig) {
+  __shared__ uint4 sk[kBsWarps][kBucketMax];
+  __shared__ uint32_t sc[kBsWarps][256];
+  constexpr int kPer = kBucketMax / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint4* k = sk[warp];
+  uint32_t* c = sc[warp];
+  for (uint32_t b = blockIdx.x * kBsWarps + warp; b < kBuckets; b += gridDim.x * kBsWarps) {
+    const uint32_t o = off[b], m = off[b + 1] - o;
+    if (m <= 1) continue;
+    bool to_big = m > kBucketMax;
+    if (!to_big) {
+      uint4 v[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) c[lane * kPer + q] = 0;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q)
+        if (lane + 32 * q < (int)m) v[q] = pairs[o + lane + 32 * q];
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < kPer; ++q)
+        if (lane + 32 * q < (int)m) atomicAdd(&c[(v[q].x >> 16) & 0xffu], 1u);
+      __syncwarp();
+      uint32_t cnt[kPer], sum = 0;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        cnt[q] = c[lane * kPer + q];
+        sum += cnt[q];
+      }
+      uint32_t x = sum;
+#pragma unroll
+      for (int s = 1; s < 32; s <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, s);
+        if (lane >= s) x += y;
+      }
+      uint32_t run = x - sum;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        c[lane * kPer + q] = run;
+        run += cnt[q];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < kPer; ++q)
+        if (lane + 32 * q < (int)m) k[atomicAdd(&c[(v[q].x >> 16) & 0xffu], 1u)] = v[q];
+      __syncwarp();
+      // c[d] is now the end of digit d's run; runs of two or more are sorted
+      bool too_long = false;
+      uint32_t start = lane == 0 ? 0u : c[lane * kPer - 1];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const uint32_t end = c[lane * kPer + q];
+        if (end - start > kRunMax) {
+          too_long = true;
+        } else {
+          for (uint32_t i = start + 1; i < end; ++i) {
+            const uint4 t = k[i];
+            uint32_t j = i;
+            while (j > start && tail_greater(k[j - 1], t)) {
+              k[j] = k[j - 1];
+              --j;
+            }
+            k[j] = t;
+          }
+        }
+        start = end;
+      }
+      to_big = __any_sync(0xffffffffu, too_long);
+      __syncwarp();
+      if (!to_big) {
+        for (uint32_t i = lane; i < m; i += 32) pairs[o + i] = k[i];
+        __syncwarp();
+        continue;
+      }
+    }
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(nbig, m);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (uint32_t i = lane; i < m; i += 32) big[base + i] = pairs[o + i];
+  }
+}
+
+// Digit counts of the first key_bytes bytes of big[0 .. *nbig).
+__global__ void __launch_bounds__(256) k_count_big(const uint4* __restrict__ big, const uint32_t* __restrict__ nbig,
+                                                   uint32_t key_bytes, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t h[12 * 256];
+  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x) h[x] = 0;
+  __syncthreads();
+  const uint64_t n = *nbig;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint4 p = big[i];
+    const uint32_t w[3] = {p.x, p.y, p.z};
+    for (uint32_t j = 0; j < key_bytes; ++j) atomicAdd(&h[j * 256 + ((w[j >> 2] >> (8 * (j & 3))) & 0xffu)], 1u);
+  }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x)
+    if (h[x]) atomicAdd(&counts[x], h[x]);
+}
+
+// first[b] = position of the first pair of prefix b in the sorted fallback
+// array (written only for the prefixes it holds).
+__global__ void __launch_bounds__(256) k_big_first(const uint4* __restrict__ sorted, const uint32_t* __restrict__ nbig,
+                                                   uint32_t* __restrict__ first) {
+  const uint64_t n = *nbig;
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = pair_prefix(sorted[j]);
+    if (j == 0 || pair_prefix(sorted[j - 1]) != p) first[p] = (uint32_t)j;
+  }
+}
+
+// The sorted fallback pairs back into their buckets' places: the j-th of
+// them is the (j - first[b])-th pair of bucket b.
+__global__ void __launch_bounds__(256) k_scatter_big(const uint4* __restrict__ sorted, const uint32_t* __restrict__ nbig,
+                                                     const uint32_t* __restrict__ off,
+                                                     const uint32_t* __restrict__ first, uint4* __restrict__ pairs) {
+  const uint64_t n = *nbig;
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint4 q = sorted[j];
+    const uint32_t b = pair_prefix(q);
+    pairs[(uint64_t)off[b] + (j - first[b])] = q;
+  }
 }
 
 }  // namespace
@@ -387,7 +565,7 @@ void rs_pass8(dpg_ctx& ctx, const uint2* in, uint2* out, uint64_t n, uint32_t by
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   TraceScope ts(ctx, SWAP ? "k_rs_onesweep8_swap" : "k_rs_onesweep8", st);
   kern<<<ntiles, kRsThreads, smem, st>>>(in, out, n, byte, counts + 256 * byte, status, tile_ctr, ctx.d_err,
-                                         ctx.wait_cycles, gword);
+                                         ctx.wait_cycles, gword, nullptr);
   ctx.launches++;
 }
 
@@ -453,28 +631,109 @@ uint8_t* run_radix_pairs8(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, u
   return radix_pairs<uint2>(ctx, a, b, scan, n, key_bytes, st, status);
 }
 
+size_t sort_keyptr_tmp_bytes(uint64_t n, uint32_t key_bytes) {
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  if (key_bytes <= 2) return al(n * 16);
+  return 2 * al(n * 16) + al(((size_t)2 * kBuckets + 2 + 12 * 256) * 4);  // + off, nbig, first, counts
+}
+
+// Phases 1 and 2 of §3 into `pairs`.  Keys of at most two bytes: that many
+// LSD passes.  Longer keys: two LSD passes on bytes 1 and 0 leave the pairs
+// in buckets of equal two-byte prefix, each in rid order; every bucket of up
+// to kBucketMax pairs is then sorted in place on key bytes 2.. and the rid
+// (k_bucket_sort).  The pairs of the other buckets (ties, skewed keys) are
+// appended, a bucket at a time, to one array that the full LSD sort orders
+// (every key byte: its passes read the pair count on the device, so nothing
+// waits for the host), and are then put back in their buckets' places.
 int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, uint32_t key_bytes, uint8_t* pairs,
                     uint8_t* tmp, uint8_t* scan, cudaStream_t st) {
   if (n == 0) return DPG_OK;
-  // an even number of passes ends where it started
-  uint8_t* start = (key_bytes % 2 == 0) ? pairs : tmp;
-  uint8_t* other = (key_bytes % 2 == 0) ? tmp : pairs;
-  if (key_bytes == 0 || key_bytes > 12) return DPG_EINVAL;
+  if (key_bytes == 0 || key_bytes > 12 || n > kCountMask) return DPG_EINVAL;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const bool buckets = key_bytes > 2;
+  // keys of one or two bytes: an even number of passes ends where it started
+  uint8_t* start = (!buckets && key_bytes % 2 == 1) ? tmp : pairs;
+  uint8_t* other = start == pairs ? tmp : pairs;
   uint32_t* counts = radix_counts(scan);
   cudaError_t e = cudaMemsetAsync(counts, 0, 12 * 256 * 4, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  const uint32_t lsd_bytes = buckets ? 2u : key_bytes;
   {
     TraceScope ts(ctx, "k_extract_pairs", st);
     const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx.sms * 8);
     if (rec % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 4 == 0)
-      k_extract_pairs<true><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, reinterpret_cast<uint4*>(start), counts);
+      k_extract_pairs<true><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, lsd_bytes, reinterpret_cast<uint4*>(start),
+                                                  counts);
     else
-      k_extract_pairs<false><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, reinterpret_cast<uint4*>(start), counts);
+      k_extract_pairs<false><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, lsd_bytes, reinterpret_cast<uint4*>(start),
+                                                   counts);
     ctx.launches++;
   }
   int status = DPG_OK;
-  run_radix_pairs(ctx, start, other, scan, n, key_bytes, st, &status);
-  return status;
+  run_radix_pairs(ctx, start, other, scan, n, lsd_bytes, st, &status);
+  if (status != DPG_OK || !buckets) return status;
+
+  uint4* p4 = reinterpret_cast<uint4*>(pairs);
+  uint4* A = reinterpret_cast<uint4*>(tmp);
+  uint4* C = reinterpret_cast<uint4*>(tmp + al(n * 16));
+  uint32_t* off = reinterpret_cast<uint32_t*>(tmp + 2 * al(n * 16));
+  uint32_t* nbig = off + kBuckets + 1;
+  uint32_t* first = nbig + 1;
+  uint32_t* counts_big = first + kBuckets;
+  const int grid = ctx.sms * 8;
+  {
+    TraceScope ts(ctx, "k_bucket_bounds", st);
+    k_bucket_bounds<<<grid, 256, 0, st>>>(p4, n, off);
+    ctx.launches++;
+  }
+  e = cudaMemsetAsync(nbig, 0, 4, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  {
+    TraceScope ts(ctx, "k_bucket_sort", st);
+    k_bucket_sort<<<grid, kBsWarps * 32, 0, st>>>(p4, off, C, nbig);
+    ctx.launches++;
+  }
+  // the fallback for the large buckets (no pairs at all for most keys)
+  e = cudaMemsetAsync(counts_big, 0, 12 * 256 * 4, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  {
+    TraceScope ts(ctx, "k_count_big", st);
+    k_count_big<<<ctx.sms * 2, 256, 0, st>>>(C, nbig, key_bytes, counts_big);
+    ctx.launches++;
+  }
+  uint32_t* tile_ctr = counts + 12 * 256;
+  uint32_t* tile_status = reinterpret_cast<uint32_t*>(scan + 16384);
+  const uint32_t ntiles_max = (uint32_t)((n + rs_tile<uint4>() - 1) / rs_tile<uint4>());
+  const size_t smem = rs_tile<uint4>() * sizeof(uint4);
+  auto kern = k_rs_onesweep<uint4, false, true>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  uint4* a = C;
+  uint4* b = A;
+  for (int byte = (int)key_bytes - 1; byte >= 0; --byte) {
+    e = cudaMemsetAsync(tile_status, 0, (size_t)ntiles_max * 256 * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+    {
+      TraceScope ts(ctx, "k_rs_onesweep_big", st);
+      kern<<<ctx.sms * kRsMinBlocks, kRsThreads, smem, st>>>(a, b, 0, (uint32_t)byte, counts_big + 256 * byte,
+                                                            tile_status, tile_ctr, ctx.d_err, ctx.wait_cycles,
+                                                            nullptr, nbig);
+    }
+    ctx.launches++;
+    std::swap(a, b);
+  }
+  {
+    TraceScope ts(ctx, "k_big_first", st);
+    k_big_first<<<ctx.sms * 2, 256, 0, st>>>(a, nbig, first);
+    ctx.launches++;
+  }
+  {
+    TraceScope ts(ctx, "k_scatter_big", st);
+    k_scatter_big<<<ctx.sms * 2, 256, 0, st>>>(a, nbig, off, first, p4);
+    ctx.launches++;
+  }
+  e = cudaGetLastError();
+  return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "sort launch");
 }
 
 }  // namespace dpg

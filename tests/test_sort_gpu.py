@@ -48,6 +48,36 @@ def test_sort_keyptr_matches_oracle(ctx, n, rec, key_bytes):
         assert np.array_equal(got.cpu().numpy(), want)
 
 
+def bucket_mix(rec, seed):
+    """Records whose two-byte key prefixes make buckets of chosen sizes (the
+    bucket stage sorts buckets of up to 256 pairs in place and sends larger
+    ones through the full LSD fallback), with whole keys repeated inside
+    buckets so that ties fall back on rid order, rows shuffled."""
+    rng = np.random.default_rng(seed)
+    sizes = [1, 2, 3, 4, 5, 31, 32, 33, 128, 129, 255, 256, 257, 258, 511, 1000, 5000]
+    prefixes = rng.choice(65536, size=len(sizes), replace=False)
+    n_rand = 40_000
+    n = sum(sizes) + n_rand
+    src = rng.integers(0, 256, size=(n, rec), dtype=np.uint8)
+    at = 0
+    for size, pre in zip(sizes, prefixes):
+        src[at:at + size, 0] = pre >> 8
+        src[at:at + size, 1] = pre & 0xff
+        if size > 3:  # a run of equal keys inside the bucket
+            src[at + 1:at + 1 + size // 3, 2:10] = src[at, 2:10]
+        at += size
+    return src[rng.permutation(n)].copy()
+
+
+@pytest.mark.parametrize("rec,key_bytes", [(16, 10), (12, 12), (16, 3), (16, 2), (16, 1), (100, 10)])
+def test_sort_bucket_sizes(ctx, rec, key_bytes):
+    src = bucket_mix(rec, 11 + key_bytes)
+    want = oracle.sort_keyptr(src, key_bytes)
+    got = ctx.sort_keyptr(to_dev(src), key_bytes)
+    ctx.sync()
+    assert np.array_equal(got.cpu().numpy(), want)
+
+
 def test_sort_all_equal_keys(ctx):
     n, rec = 50_001, 16
     src = synth.records(n, rec, 9).copy()

@@ -888,7 +888,7 @@ def main():
             "small_records": small,
             "full_sort": {"ms_per_sort": round(ms_sortall, 4), "keyptr_sort_ms": round(ms_keyptr, 4),
                           "records_per_s": round(world * n / (ms_sortall * 1e-3), 1),
-                          "what": "dpg_sort_records: extract pairs + stable 10-pass LSD radix sort + DPG copy"},
+                          "what": "dpg_sort_records: extract pairs, LSD passes on key bytes 1 and 0, per-bucket sort of the rest, DPG copy"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": ncu_traffic(dom, n, rec, plan),

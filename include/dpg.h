@@ -115,18 +115,17 @@ dpg_status dpg_sort_copy_direct(dpg_ctx* ctx, const void* pairs, size_t pair_str
  * by key as unsigned byte strings, equal keys in rid order.  `pairs` receives
  * n_src pairs of 16 bytes: key bytes, zero padding to byte 12, int32 rid at
  * byte 12 (the layout dpg_sort_copy reads with pair_stride 16, rid_off 12).
- * Stable LSD radix sort, one key byte per pass.
+ * Stable LSD radix passes on key bytes 1 and 0 (one byte per pass), then each
+ * bucket of equal two-byte prefix sorted on the rest of the key and the rid;
+ * buckets of more than 256 pairs (ties, skewed keys) go through the full LSD
+ * sort in one cooperative launch.  Context scratch: about 32 bytes per record.
  */
 dpg_status dpg_sort_keyptr(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes, size_t key_bytes,
                            void* pairs, void* stream);
 
-/* The whole §3 sort: dst[i] = the record of rank i in (key, rid) order; the
- * result of dpg_sort_keyptr followed by dpg_sort_copy (DPG record
- * retrieval).  Only the rid order is needed here, so phase 2 sorts 8-byte
- * (key word, rid) pairs instead of the 16-byte key-pointer pairs: the key in
- * 4-byte groups from its least significant end, each group's word swapped in
- * by rid when its passes begin.  Context scratch: about 16 + 4 *
- * (ceil(key_bytes / 4) - 1) bytes per record. */
+/* The whole §3 sort: dst[i] = the record of rank i in (key, rid) order, i.e.
+ * dpg_sort_keyptr followed by dpg_sort_copy (DPG record retrieval).  Context
+ * scratch: about 48 bytes per record. */
 dpg_status dpg_sort_records(dpg_ctx* ctx, const void* src, size_t n_src, size_t rec_bytes, size_t key_bytes,
                             void* dst, void* stream);
 

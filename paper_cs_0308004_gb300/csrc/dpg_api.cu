@@ -346,17 +346,16 @@ dpg_status dpg_sort_records(dpg_ctx* c, const void* src, size_t n_src, size_t re
   if (s != DPG_OK || n_src == 0) return (dpg_status)s;
   if (rec > dpg::kMaxDpgRecBytes || overlaps(src, n_src * rec, dst, n_src * rec)) return DPG_EINVAL;
   DeviceGuard g(c->device);
-  // the sort ends in 8-byte (key word, rid) pairs; the copy phase reads their rids
-  const size_t bt = al256(dpg::sort_pairs8_tmp_bytes(n_src, (uint32_t)key_bytes)), bs = dpg::sort_scan_bytes(n_src);
-  if ((s = dpg::ensure_aux(*c, bt + bs))) return (dpg_status)s;
-  uint8_t* tmp = static_cast<uint8_t*>(c->aux);
+  const size_t bp = al256(n_src * 16), bt = al256(dpg::sort_keyptr_tmp_bytes(n_src, (uint32_t)key_bytes)),
+               bs = dpg::sort_scan_bytes(n_src);
+  if ((s = dpg::ensure_aux(*c, bp + bt + bs))) return (dpg_status)s;
+  uint8_t* pairs = static_cast<uint8_t*>(c->aux);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  uint8_t* pairs = nullptr;
-  s = dpg::run_sort_pairs8(*c, static_cast<const uint8_t*>(src), n_src, (uint32_t)rec, (uint32_t)key_bytes, tmp,
-                           tmp + bt, st, &pairs);
+  s = dpg::run_sort_keyptr(*c, static_cast<const uint8_t*>(src), n_src, (uint32_t)rec, (uint32_t)key_bytes, pairs,
+                           pairs + bp, pairs + bp + bt, st);
   if (s != DPG_OK) return (dpg_status)s;
   dpg::Retrieval r{static_cast<const uint8_t*>(src), n_src, (uint32_t)rec, n_src,
-                   dpg::RidSpec{pairs + 4, 8}, static_cast<uint8_t*>(dst), st};
+                   dpg::RidSpec{pairs + 12, 16}, static_cast<uint8_t*>(dst), st};
   return (dpg_status)dpg::run_dpg(*c, r, dpg::choose_plan(*c, r));
 }
 

@@ -184,12 +184,6 @@ uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, ui
 uint8_t* run_radix_pairs8(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
                           cudaStream_t st, int* status);
 
-// Phases 1-2 of the §3 sort (dpg_sort.cu) on 8-byte (key group word, rid)
-// pairs, for callers that need the rid order only: *final8 = the sorted
-// pairs (rid at byte 4) inside tmp, which holds sort_pairs8_tmp_bytes(n, K).
-size_t sort_pairs8_tmp_bytes(uint64_t n, uint32_t key_bytes);
-int run_sort_pairs8(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, uint32_t key_bytes, uint8_t* tmp,
-                    uint8_t* scan, cudaStream_t st, uint8_t** final8);
 // Phases 1-2 of the §3 sort (dpg_sort.cu): sorted 16-byte key-pointer pairs;
 // tmp holds sort_keyptr_tmp_bytes(n, key_bytes), scan sort_scan_bytes(n).
 size_t sort_keyptr_tmp_bytes(uint64_t n, uint32_t key_bytes);

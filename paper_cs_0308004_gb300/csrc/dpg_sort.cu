@@ -20,10 +20,8 @@
 // each digit's pairs as one contiguous piece at digit base + earlier tiles'
 // count.
 //
-// dpg_sort_keyptr sorts 16-byte key-pointer pairs.  dpg_sort_records needs
-// only the order of the rids, so it sorts 8-byte (key word, rid) pairs: the
-// key in 4-byte groups from its least significant end, the pass that starts
-// a group swapping that group's word in from a per-rid side array.
+// Keys longer than two bytes take only the passes on bytes 1 and 0; each
+// bucket of equal two-byte prefix is then sorted on its own (run_sort_keyptr).
 #include <algorithm>
 
 #include "dpg_device.cuh"
@@ -46,6 +44,7 @@ template <class E> __host__ __device__ constexpr int rs_items() { return sizeof(
 template <class E> __host__ __device__ constexpr int rs_look_win() { return sizeof(E) == 16 ? 8 : 1; }
 // pairs per tile
 template <class E> __host__ __device__ constexpr uint32_t rs_tile() { return kRsThreads * rs_items<E>(); }
+inline uint32_t ntiles_of(uint64_t n) { return (uint32_t)((n + rs_tile<uint4>() - 1) / rs_tile<uint4>()); }
 
 // Phase 1: pairs[i] = (key of record i, zero pad, i).  WORDS: records and
 // the table are 4-byte aligned, so the key is read as ceil(key_bytes/4)
@@ -86,57 +85,6 @@ __global__ void __launch_bounds__(256)
     if (h[x]) atomicAdd(&counts[x], h[x]);
 }
 
-// Phase 1 for the 8-byte sort: the key of record i in groups of 4 bytes
-// from its least significant end (group g = bytes [K - 4g - 4, K - 4g),
-// clipped at 0; byte j at bits 8 * (j % 4) of its group's word).  pairs[i] =
-// (group 0's word, i), side1/side2[i] = group 1's and group 2's words (the
-// passes that start those groups read them; null when the key has no such
-// group), and the digit counts of every key byte (counts[j * 256 + d], zero
-// on entry).
-template <bool WORDS>
-__global__ void __launch_bounds__(256)
-    k_extract_pairs8(const uint8_t* __restrict__ src, uint64_t n, uint32_t rec, uint32_t key_bytes,
-                     uint2* __restrict__ pairs, uint32_t* __restrict__ side1, uint32_t* __restrict__ side2,
-                     uint32_t* __restrict__ counts) {
-  __shared__ uint32_t h[12 * 256];
-  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x) h[x] = 0;
-  __syncthreads();
-  const uint32_t nw = (key_bytes + 3) / 4;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint8_t* r = src + i * rec;
-    uint32_t w[3] = {0u, 0u, 0u};
-    if (WORDS) {
-      const uint32_t* rw = reinterpret_cast<const uint32_t*>(r);
-#pragma unroll
-      for (uint32_t j = 0; j < 3; ++j)
-        if (j < nw) {
-          const uint32_t keep = key_bytes >= 4 * (j + 1) ? 32u : 8u * (key_bytes - 4 * j);
-          const uint32_t v = __ldg(rw + j);
-          w[j] = keep == 32u ? v : (v & ((1u << keep) - 1u));
-        }
-    } else {
-#pragma unroll
-      for (uint32_t b = 0; b < 12; ++b)
-        if (b < key_bytes) w[b >> 2] |= (uint32_t)__ldg(r + b) << (8 * (b & 3));
-    }
-    // group g holds bytes [lo, hi): the bytes of words lo/4 .. (hi-1)/4 in range
-    uint32_t gw[3] = {0u, 0u, 0u};
-#pragma unroll
-    for (uint32_t g = 0; g < 3; ++g) {
-      const int hi = (int)key_bytes - 4 * (int)g, lo = hi - 4 < 0 ? 0 : hi - 4;
-      if (hi <= 0) break;
-      for (int j = lo; j < hi; ++j) gw[g] |= w[j >> 2] & (0xffu << (8 * (j & 3)));
-    }
-    pairs[i] = make_uint2(gw[0], (uint32_t)i);
-    if (side1) side1[i] = gw[1];
-    if (side2) side2[i] = gw[2];
-    for (uint32_t j = 0; j < key_bytes; ++j) atomicAdd(&h[j * 256 + ((w[j >> 2] >> (8 * (j & 3))) & 0xffu)], 1u);
-  }
-  __syncthreads();
-  for (uint32_t x = threadIdx.x; x < key_bytes * 256; x += blockDim.x)
-    if (h[x]) atomicAdd(&counts[x], h[x]);
-}
-
 // Key byte `byte` of a pair: 16-byte pairs hold up to 12 key bytes in words
 // x, y, z; 8-byte pairs (the DPG-sort join's) up to 4 in x, the rid in y.
 __device__ __forceinline__ uint32_t pair_digit(const uint4& p, uint32_t byte) {
@@ -149,27 +97,36 @@ __device__ __forceinline__ uint32_t pair_digit(const uint2& p, uint32_t byte) {
 
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagPrefix = 2u << 30, kCountMask = (1u << 30) - 1;
 
-// One stable pass on key byte `byte`.  Tiles are numbered in the order CTAs
-// claim them (tile_ctr), so a tile only waits for tiles whose CTAs already
-// run.  E: uint4 (16-byte pairs) or uint2 (8-byte pairs).  SWAP (8-byte
-// pairs): the pass starts a new key group, so each pair's key word is first
-// replaced by gword[rid] (that group's word).  DEVN: the pair count is
-// *n_dev (known only on the device) and each CTA claims tiles until none is
-// left; a CTA finishes a tile before it claims the next, so the waits stay
-// on tiles of running CTAs.
-template <class E, bool SWAP = false, bool DEVN = false>
-__global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
-    k_rs_onesweep(const E* __restrict__ in, E* __restrict__ out, uint64_t n_arg, uint32_t byte,
-                  const uint32_t* __restrict__ digit_count, uint32_t* status, uint32_t* tile_ctr, int* err,
-                  long long wait_limit, const uint32_t* __restrict__ gword = nullptr,
-                  const uint32_t* __restrict__ n_dev = nullptr) {
-  __shared__ uint16_t whist[kRsWarps][256];  // pairs of digit d in warp w's share of the tile
-  __shared__ uint16_t wslot[kRsWarps][256];  // tile slot of warp w's first pair of digit d
-  __shared__ uint32_t s_base[256];           // output position of the pass's first pair of digit d
-  __shared__ uint32_t s_gpos[256];           // output position of this tile's first pair of digit d
-  __shared__ uint32_t s_toff[256];           // tile slot of this tile's first pair of digit d
-  __shared__ uint32_t s_wsum[8];
-  __shared__ uint32_t s_tile;
+// Shared state of one CTA's tile in a radix pass.
+struct RsShared {
+  uint16_t whist[kRsWarps][256];  // pairs of digit d in warp w's share of the tile
+  uint16_t wslot[kRsWarps][256];  // tile slot of warp w's first pair of digit d
+  uint32_t s_base[256];           // output position of the pass's first pair of digit d
+  uint32_t s_gpos[256];           // output position of this tile's first pair of digit d
+  uint32_t s_toff[256];           // tile slot of this tile's first pair of digit d
+  uint32_t s_wsum[8];
+  uint32_t s_tile;
+  int s_ok;
+};
+
+// Claim the CTA's next tile of a pass (its number in sh.s_tile) and clear
+// the per-warp counts.
+__device__ __forceinline__ uint32_t rs_claim(uint32_t* tile_ctr, RsShared& sh) {
+  if (threadIdx.x == 0) sh.s_tile = atomicAdd(tile_ctr, 1u);
+  for (uint32_t x = threadIdx.x; x < kRsWarps * 128; x += kRsThreads) reinterpret_cast<uint32_t*>(&sh.whist[0][0])[x] = 0;
+  __syncthreads();
+  return sh.s_tile;
+}
+
+// One tile t of a stable pass on key byte `byte` (tiles are numbered in the
+// order CTAs claim them, so a tile only waits for tiles whose CTAs already
+// run).  E: uint4 (16-byte pairs) or uint2 (8-byte pairs).  CG: the input was written
+// earlier in the same launch, so it is read from L2 (ld.global.cg), never
+// through a cache that may hold older lines.
+template <class E, bool CG = false>
+__device__ __forceinline__ void rs_tile_body(const E* __restrict__ in, E* __restrict__ out, uint64_t n, uint32_t byte,
+                                             const uint32_t* __restrict__ digit_count, uint32_t* status, uint32_t t,
+                                             int* err, long long wait_limit, RsShared& sh) {
   constexpr int kItems = rs_items<E>();
   constexpr uint32_t kTile = rs_tile<E>();
   static_assert(kTile <= 65536, "tile slots are 16-bit");
@@ -177,14 +134,6 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
   E* sbuf = reinterpret_cast<E*>(sraw);  // kTile pairs
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  const uint64_t n = DEVN ? (uint64_t)*n_dev : n_arg;
-  const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
-  for (;;) {
-  if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
-  for (uint32_t x = threadIdx.x; x < kRsWarps * 128; x += kRsThreads) reinterpret_cast<uint32_t*>(&whist[0][0])[x] = 0;
-  __syncthreads();
-  const uint32_t t = s_tile;
-  if (DEVN && t >= ntiles) break;
   const uint64_t base = (uint64_t)t * kTile;
   // digit bases of this pass: exclusive scan of the digit counts (warp 1, 8 per lane)
   if (warp == 1) {
@@ -203,7 +152,7 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
     uint32_t run = x - sum;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      s_base[lane * 8 + j] = run;
+      sh.s_base[lane * 8 + j] = run;
       run += c[j];
     }
   }
@@ -218,12 +167,7 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
   // which would otherwise hold each load back until the previous round ends
 #pragma unroll
   for (int k = 0; k < kItems; ++k)
-    if ((uint32_t)k * 32 < rem) v[k] = inp[k * 32];
-  if constexpr (SWAP) {
-#pragma unroll
-    for (int k = 0; k < kItems; ++k)
-      if ((uint32_t)k * 32 < rem) v[k].x = gword[v[k].y];
-  }
+    if ((uint32_t)k * 32 < rem) v[k] = CG ? __ldcg(inp + k * 32) : inp[k * 32];
   // stable in-warp ranks: round k's peers (valid lanes with the same digit)
   // are the AND of eight ballots, one per digit bit; the lane's rank is the
   // warp's count of that digit in earlier rounds plus its peers below it
@@ -238,9 +182,9 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
       peers &= __ballot_sync(0xffffffffu, bit != 0u) ^ (bit - 1u);
     }
     const uint32_t before = __popc(peers & lt);
-    const uint32_t prior = ok ? whist[warp][d] : 0u;
+    const uint32_t prior = ok ? sh.whist[warp][d] : 0u;
     __syncwarp();
-    if (ok && before == 0) whist[warp][d] = (uint16_t)(prior + __popc(peers));
+    if (ok && before == 0) sh.whist[warp][d] = (uint16_t)(prior + __popc(peers));
     __syncwarp();
     if (k & 1) rank2[k >> 1] |= (prior + before) << 16;
     else rank2[k >> 1] = prior + before;
@@ -249,7 +193,7 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
   const uint32_t dg = threadIdx.x & 255;
   uint32_t cnt = 0;  // the tile's count of digit dg
 #pragma unroll
-  for (int w = 0; w < kRsWarps; ++w) cnt += whist[w][dg];
+  for (int w = 0; w < kRsWarps; ++w) cnt += sh.whist[w][dg];
   if (threadIdx.x < 256) {
     // publish this tile's count of digit dg, then look back over earlier tiles
     volatile uint32_t* st = status;
@@ -286,7 +230,7 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
       }
       st[(uint64_t)t * 256 + dg] = kFlagPrefix | (excl + cnt);
     }
-    s_gpos[dg] = s_base[dg] + excl;
+    sh.s_gpos[dg] = sh.s_base[dg] + excl;
   } else {
     // meanwhile the upper 256 threads lay out the tile: exclusive scan of the
     // counts over digits, then each warp's first slot per digit
@@ -296,15 +240,15 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    if (lane == 31) s_wsum[warp - 8] = x;
+    if (lane == 31) sh.s_wsum[warp - 8] = x;
     asm volatile("bar.sync 1, 256;" ::: "memory");
     uint32_t off = x - cnt;
-    for (int w = 0; w < warp - 8; ++w) off += s_wsum[w];
-    s_toff[dg] = off;
+    for (int w = 0; w < warp - 8; ++w) off += sh.s_wsum[w];
+    sh.s_toff[dg] = off;
 #pragma unroll
     for (int w = 0; w < kRsWarps; ++w) {
-      wslot[w][dg] = (uint16_t)off;
-      off += whist[w][dg];
+      sh.wslot[w][dg] = (uint16_t)off;
+      off += sh.whist[w][dg];
     }
   }
   __syncthreads();
@@ -312,7 +256,7 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
   for (int k = 0; k < kItems; ++k) {
     if ((uint32_t)k * 32 < rem) {
       const uint32_t d = pair_digit(v[k], byte);
-      sbuf[wslot[warp][d] + ((rank2[k >> 1] >> (16 * (k & 1))) & 0xffffu)] = v[k];
+      sbuf[sh.wslot[warp][d] + ((rank2[k >> 1] >> (16 * (k & 1))) & 0xffffu)] = v[k];
     }
   }
   __syncthreads();
@@ -320,10 +264,83 @@ __global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
   for (uint32_t p = threadIdx.x; p < tn; p += kRsThreads) {
     const E q = sbuf[p];
     const uint32_t d = pair_digit(q, byte);
-    out[(uint64_t)(uint32_t)(s_gpos[d] + (p - s_toff[d]))] = q;
+    out[(uint64_t)(uint32_t)(sh.s_gpos[d] + (p - sh.s_toff[d]))] = q;
   }
-  if (!DEVN) break;
-  __syncthreads();  // the next tile reuses shared memory
+}
+
+// One stable pass, one tile per CTA (the grid has a CTA per tile).
+template <class E>
+__global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
+    k_rs_onesweep(const E* __restrict__ in, E* __restrict__ out, uint64_t n, uint32_t byte,
+                  const uint32_t* __restrict__ digit_count, uint32_t* status, uint32_t* tile_ctr, int* err,
+                  long long wait_limit) {
+  __shared__ RsShared sh;
+  const uint32_t t = rs_claim(tile_ctr, sh);
+  rs_tile_body<E>(in, out, n, byte, digit_count, status, t, err, wait_limit, sh);
+}
+
+// Wait (bounded) until every CTA of the grid has arrived at barrier number
+// `round` (counter *ctr, zero before the launch); false after the limit.
+__device__ __forceinline__ bool grid_barrier(uint32_t* ctr, uint32_t round, long long limit, RsShared& sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    bool ok;
+    const uint32_t target = round * gridDim.x;
+    wait_word_bounded(ctr, limit, &ok, [target](uint32_t x) { return x >= target; });
+    __threadfence();
+    sh.s_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  return sh.s_ok != 0;
+}
+
+// The whole LSD sort (key bytes key_bytes-1 .. 0) of a[0 .. *n_dev) in one
+// cooperative launch (every CTA resident): pass p reads a or b in turn,
+// claims tiles from ctrs[p] and publishes into status region p % 2 (of
+// region_words words each); a grid barrier (counter ctrs[key_bytes]) orders
+// the clearing of region 0 before pass 0 and each pass before the next, and
+// each pass clears the region the next one uses.  The result is in a for an
+// even key_bytes, else in b.  counts: key_bytes x 256 digit counts; ctrs:
+// key_bytes + 1 words, zero before the launch.  No pairs: the launch returns
+// at once.
+__global__ void __launch_bounds__(kRsThreads, kRsMinBlocks)
+    k_rs_passes(uint4* a, uint4* b, const uint32_t* __restrict__ n_dev, uint32_t key_bytes,
+                const uint32_t* __restrict__ counts, uint32_t* status, uint64_t region_words, uint32_t* ctrs,
+                int* err, long long wait_limit) {
+  __shared__ RsShared sh;
+  const uint64_t n = *n_dev;
+  const uint32_t ntiles = (uint32_t)((n + rs_tile<uint4>() - 1) / rs_tile<uint4>());
+  if (ntiles == 0) return;
+  for (uint64_t x = blockIdx.x * (uint64_t)kRsThreads + threadIdx.x; x < (uint64_t)ntiles * 256;
+       x += (uint64_t)gridDim.x * kRsThreads)
+    status[x] = 0;
+  if (!grid_barrier(ctrs + key_bytes, 1, wait_limit, sh)) {
+    if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+    return;
+  }
+  for (uint32_t p = 0; p < key_bytes; ++p) {
+    const uint32_t byte = key_bytes - 1 - p;
+    const uint4* in = (p & 1) ? b : a;
+    uint4* out = (p & 1) ? a : b;
+    uint32_t* region = status + (p & 1) * region_words;
+    if (p + 1 < key_bytes) {  // the next pass's region: last used two passes ago
+      uint32_t* next = status + ((p + 1) & 1) * region_words;
+      for (uint64_t x = blockIdx.x * (uint64_t)kRsThreads + threadIdx.x; x < (uint64_t)ntiles * 256;
+           x += (uint64_t)gridDim.x * kRsThreads)
+        next[x] = 0;
+    }
+    for (;;) {
+      const uint32_t t = rs_claim(ctrs + p, sh);
+      if (t >= ntiles) break;
+      rs_tile_body<uint4, true>(in, out, n, byte, counts + 256 * byte, region, t, err, wait_limit, sh);
+      __syncthreads();
+    }
+    if (p + 1 < key_bytes && !grid_barrier(ctrs + key_bytes, p + 2, wait_limit, sh)) {
+      if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+      return;
+    }
   }
 }
 
@@ -548,79 +565,6 @@ uint8_t* radix_pairs(dpg_ctx& ctx, uint8_t* a_, uint8_t* b_, uint8_t* scan, uint
 
 uint32_t* radix_counts(uint8_t* scan) { return reinterpret_cast<uint32_t*>(scan); }
 
-size_t sort_pairs8_tmp_bytes(uint64_t n, uint32_t key_bytes) {
-  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const uint32_t groups = (key_bytes + 3) / 4;
-  return 2 * al(n * 8) + (groups > 1 ? groups - 1 : 0) * al(n * 4);
-}
-
-namespace {
-
-template <bool SWAP>
-void rs_pass8(dpg_ctx& ctx, const uint2* in, uint2* out, uint64_t n, uint32_t byte, const uint32_t* counts,
-              uint32_t* status, uint32_t* tile_ctr, const uint32_t* gword, cudaStream_t st) {
-  const uint32_t ntiles = (uint32_t)((n + rs_tile<uint2>() - 1) / rs_tile<uint2>());
-  const size_t smem = rs_tile<uint2>() * sizeof(uint2);
-  auto kern = k_rs_onesweep<uint2, SWAP>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  TraceScope ts(ctx, SWAP ? "k_rs_onesweep8_swap" : "k_rs_onesweep8", st);
-  kern<<<ntiles, kRsThreads, smem, st>>>(in, out, n, byte, counts + 256 * byte, status, tile_ctr, ctx.d_err,
-                                         ctx.wait_cycles, gword, nullptr);
-  ctx.launches++;
-}
-
-}  // namespace
-
-// Phases 1 and 2 of §3 on 8-byte pairs (the rid order only): the LSD passes
-// run over (group word, rid) pairs, group 0 being the key's 4 least
-// significant bytes; the first pass of group g >= 1 swaps in side[g][rid]
-// (stability keeps the order the bytes already sorted gave, and no later
-// pass needs those bytes again).  *final8 = the sorted pairs (rid at byte 4)
-// inside tmp (sort_pairs8_tmp_bytes).
-int run_sort_pairs8(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, uint32_t key_bytes, uint8_t* tmp,
-                    uint8_t* scan, cudaStream_t st, uint8_t** final8) {
-  if (key_bytes == 0 || key_bytes > 12 || n > kCountMask) return DPG_EINVAL;
-  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  uint2* buf[2] = {reinterpret_cast<uint2*>(tmp), reinterpret_cast<uint2*>(tmp + al(n * 8))};
-  *final8 = tmp;
-  if (n == 0) return DPG_OK;
-  const uint32_t groups = (key_bytes + 3) / 4;
-  uint32_t* side[3] = {nullptr, nullptr, nullptr};
-  for (uint32_t g = 1; g < groups; ++g)
-    side[g] = reinterpret_cast<uint32_t*>(tmp + 2 * al(n * 8) + (g - 1) * al(n * 4));
-  uint32_t* counts = radix_counts(scan);
-  uint32_t* tile_ctr = counts + 12 * 256;
-  uint32_t* tile_status = reinterpret_cast<uint32_t*>(scan + 16384);
-  cudaError_t e = cudaMemsetAsync(counts, 0, 12 * 256 * 4, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
-  {
-    TraceScope ts(ctx, "k_extract_pairs", st);
-    const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx.sms * 8);
-    if (rec % 4 == 0 && reinterpret_cast<uintptr_t>(src) % 4 == 0)
-      k_extract_pairs8<true><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, buf[0], side[1], side[2], counts);
-    else
-      k_extract_pairs8<false><<<grid, 256, 0, st>>>(src, n, rec, key_bytes, buf[0], side[1], side[2], counts);
-    ctx.launches++;
-  }
-  int cur = 0;
-  for (int byte = (int)key_bytes - 1; byte >= 0; --byte) {
-    const uint32_t from_end = (uint32_t)((int)key_bytes - 1 - byte);
-    const uint32_t g = from_end / 4;
-    const uint32_t ntiles = (uint32_t)((n + rs_tile<uint2>() - 1) / rs_tile<uint2>());
-    e = cudaMemsetAsync(tile_status, 0, (size_t)ntiles * 256 * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, 4, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
-    if (g > 0 && from_end % 4 == 0)
-      rs_pass8<true>(ctx, buf[cur], buf[cur ^ 1], n, (uint32_t)byte, counts, tile_status, tile_ctr, side[g], st);
-    else
-      rs_pass8<false>(ctx, buf[cur], buf[cur ^ 1], n, (uint32_t)byte, counts, tile_status, tile_ctr, nullptr, st);
-    cur ^= 1;
-  }
-  *final8 = reinterpret_cast<uint8_t*>(buf[cur]);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? DPG_OK : cuda_fail(ctx, e, "sort launch");
-}
-
 uint8_t* run_radix_pairs(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, uint64_t n, uint32_t key_bytes,
                          cudaStream_t st, int* status) {
   return radix_pairs<uint4>(ctx, a, b, scan, n, key_bytes, st, status);
@@ -634,7 +578,8 @@ uint8_t* run_radix_pairs8(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, u
 size_t sort_keyptr_tmp_bytes(uint64_t n, uint32_t key_bytes) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   if (key_bytes <= 2) return al(n * 16);
-  return 2 * al(n * 16) + al(((size_t)2 * kBuckets + 2 + 12 * 256) * 4);  // + off, nbig, first, counts
+  // + off, nbig, first, digit counts, two status regions and the pass counters
+  return 2 * al(n * 16) + al(((size_t)2 * kBuckets + 2 + 12 * 256 + 2 * (size_t)ntiles_of(n) * 256 + 16) * 4);
 }
 
 // Phases 1 and 2 of §3 into `pairs`.  Keys of at most two bytes: that many
@@ -701,27 +646,33 @@ int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, 
     k_count_big<<<ctx.sms * 2, 256, 0, st>>>(C, nbig, key_bytes, counts_big);
     ctx.launches++;
   }
-  uint32_t* tile_ctr = counts + 12 * 256;
-  uint32_t* tile_status = reinterpret_cast<uint32_t*>(scan + 16384);
-  const uint32_t ntiles_max = (uint32_t)((n + rs_tile<uint4>() - 1) / rs_tile<uint4>());
+  // the LSD fallback in one cooperative launch (it returns at once when no
+  // bucket needed it)
+  const uint64_t region_words = (uint64_t)ntiles_of(n) * 256;
+  uint32_t* fstatus = counts_big + 12 * 256;
+  uint32_t* ctrs = fstatus + 2 * region_words;
+  e = cudaMemsetAsync(ctrs, 0, 16 * 4, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   const size_t smem = rs_tile<uint4>() * sizeof(uint4);
-  auto kern = k_rs_onesweep<uint4, false, true>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int blocks_per_sm = 0;
+  e = cudaFuncSetAttribute(k_rs_passes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_rs_passes, kRsThreads, smem);
+  if (e == cudaSuccess && blocks_per_sm < 1) e = cudaErrorInvalidConfiguration;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
   uint4* a = C;
   uint4* b = A;
-  for (int byte = (int)key_bytes - 1; byte >= 0; --byte) {
-    e = cudaMemsetAsync(tile_status, 0, (size_t)ntiles_max * 256 * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, 4, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
-    {
-      TraceScope ts(ctx, "k_rs_onesweep_big", st);
-      kern<<<ctx.sms * kRsMinBlocks, kRsThreads, smem, st>>>(a, b, 0, (uint32_t)byte, counts_big + 256 * byte,
-                                                            tile_status, tile_ctr, ctx.d_err, ctx.wait_cycles,
-                                                            nullptr, nbig);
-    }
+  {
+    TraceScope ts(ctx, "k_rs_passes", st);
+    uint32_t kb = key_bytes;
+    long long wl = ctx.wait_cycles;
+    void* args[] = {&a, &b, &nbig, &kb, &counts_big, &fstatus, const_cast<uint64_t*>(&region_words), &ctrs,
+                    &ctx.d_err, &wl};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_rs_passes), dim3(blocks_per_sm * ctx.sms),
+                                    dim3(kRsThreads), args, smem, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cooperative launch");
     ctx.launches++;
-    std::swap(a, b);
   }
+  if (key_bytes % 2 == 1) a = b;  // where the passes left the sorted pairs
   {
     TraceScope ts(ctx, "k_big_first", st);
     k_big_first<<<ctx.sms * 2, 256, 0, st>>>(a, nbig, first);

@@ -391,6 +391,10 @@ __global__ void __launch_bounds__(kBsWarps * 32) k_bucket_sort(uint4* __restrict
   __shared__ uint4 sk[kBsWarps][kBucketMax];
   __shared__ uint32_t sc[kBsWarps][256];
   constexpr int kPer = kBucketMax / 32;
+  static_assert(kPer == 8, "the count layout holds 8 digits per lane");
+  // digit d's count at ((d % 8) << 5) | (d / 8): lane l's digits 8l..8l+7 sit
+  // in 8 different rows of one bank, so the per-lane scan is conflict-free
+  auto ci = [](uint32_t d) { return ((d & 7u) << 5) | (d >> 3); };
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint4* k = sk[warp];
   uint32_t* c = sc[warp];
@@ -401,19 +405,19 @@ __global__ void __launch_bounds__(kBsWarps * 32) k_bucket_sort(uint4* __restrict
     if (!to_big) {
       uint4 v[kPer];
 #pragma unroll
-      for (int q = 0; q < kPer; ++q) c[lane * kPer + q] = 0;
+      for (int q = 0; q < kPer; ++q) c[(q << 5) | lane] = 0;
 #pragma unroll
       for (int q = 0; q < kPer; ++q)
         if (lane + 32 * q < (int)m) v[q] = pairs[o + lane + 32 * q];
       __syncwarp();
 #pragma unroll
       for (int q = 0; q < kPer; ++q)
-        if (lane + 32 * q < (int)m) atomicAdd(&c[(v[q].x >> 16) & 0xffu], 1u);
+        if (lane + 32 * q < (int)m) atomicAdd(&c[ci((v[q].x >> 16) & 0xffu)], 1u);
       __syncwarp();
       uint32_t cnt[kPer], sum = 0;
 #pragma unroll
       for (int q = 0; q < kPer; ++q) {
-        cnt[q] = c[lane * kPer + q];
+        cnt[q] = c[(q << 5) | lane];
         sum += cnt[q];
       }
       uint32_t x = sum;
@@ -425,20 +429,20 @@ __global__ void __launch_bounds__(kBsWarps * 32) k_bucket_sort(uint4* __restrict
       uint32_t run = x - sum;
 #pragma unroll
       for (int q = 0; q < kPer; ++q) {
-        c[lane * kPer + q] = run;
+        c[(q << 5) | lane] = run;
         run += cnt[q];
       }
       __syncwarp();
 #pragma unroll
       for (int q = 0; q < kPer; ++q)
-        if (lane + 32 * q < (int)m) k[atomicAdd(&c[(v[q].x >> 16) & 0xffu], 1u)] = v[q];
+        if (lane + 32 * q < (int)m) k[atomicAdd(&c[ci((v[q].x >> 16) & 0xffu)], 1u)] = v[q];
       __syncwarp();
       // c[d] is now the end of digit d's run; runs of two or more are sorted
       bool too_long = false;
-      uint32_t start = lane == 0 ? 0u : c[lane * kPer - 1];
+      uint32_t start = lane == 0 ? 0u : c[(7 << 5) | (lane - 1)];
 #pragma unroll
       for (int q = 0; q < kPer; ++q) {
-        const uint32_t end = c[lane * kPer + q];
+        const uint32_t end = c[(q << 5) | lane];
         if (end - start > kRunMax) {
           too_long = true;
         } else {

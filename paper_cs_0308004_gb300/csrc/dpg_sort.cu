@@ -579,11 +579,28 @@ uint8_t* run_radix_pairs8(dpg_ctx& ctx, uint8_t* a, uint8_t* b, uint8_t* scan, u
   return radix_pairs<uint2>(ctx, a, b, scan, n, key_bytes, st, status);
 }
 
+// Words of the bucketed sort's state, all zeroed by one memset before the
+// sort: the digit counts of key bytes 0 and 1, the two passes' tile
+// counters, the fallback's pair count, its digit counts and its pass
+// counters, then each of the two passes' status region.  After them: the
+// fallback's two status regions (cleared by its own launch), the bucket
+// offsets and the fallback's first position per prefix.
+struct BucketState {
+  static constexpr uint64_t kCounts = 0, kTileCtr = 3072, kNbig = 3136, kCountsBig = 3200, kCtrs = 6272,
+                            kStatus = 6400;
+  uint64_t region;  // words of one status region: 256 per tile
+  explicit BucketState(uint64_t n) : region((uint64_t)ntiles_of(n) * 256) {}
+  uint64_t zeroed() const { return kStatus + 2 * region; }
+  uint64_t fstatus() const { return zeroed(); }
+  uint64_t off() const { return fstatus() + 2 * region; }
+  uint64_t first() const { return off() + kBuckets + 1; }
+  uint64_t words() const { return first() + kBuckets; }
+};
+
 size_t sort_keyptr_tmp_bytes(uint64_t n, uint32_t key_bytes) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   if (key_bytes <= 2) return al(n * 16);
-  // + off, nbig, first, digit counts, two status regions and the pass counters
-  return 2 * al(n * 16) + al(((size_t)2 * kBuckets + 2 + 12 * 256 + 2 * (size_t)ntiles_of(n) * 256 + 16) * 4);
+  return 2 * al(n * 16) + al(BucketState(n).words() * 4);
 }
 
 // Phases 1 and 2 of §3 into `pairs`.  Keys of at most two bytes: that many
@@ -603,10 +620,14 @@ int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, 
   // keys of one or two bytes: an even number of passes ends where it started
   uint8_t* start = (!buckets && key_bytes % 2 == 1) ? tmp : pairs;
   uint8_t* other = start == pairs ? tmp : pairs;
-  uint32_t* counts = radix_counts(scan);
-  cudaError_t e = cudaMemsetAsync(counts, 0, 12 * 256 * 4, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   const uint32_t lsd_bytes = buckets ? 2u : key_bytes;
+  const BucketState bs(n);
+  uint32_t* state = reinterpret_cast<uint32_t*>(tmp + (buckets ? 2 * al(n * 16) : 0));
+  uint32_t* counts = buckets ? state + BucketState::kCounts : radix_counts(scan);
+  // the bucketed sort clears all of its small state and both passes' status
+  // regions at once
+  cudaError_t e = cudaMemsetAsync(counts, 0, buckets ? bs.zeroed() * 4 : 12 * 256 * 4, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   {
     TraceScope ts(ctx, "k_extract_pairs", st);
     const int grid = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx.sms * 8);
@@ -618,33 +639,42 @@ int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, 
                                                    counts);
     ctx.launches++;
   }
-  int status = DPG_OK;
-  run_radix_pairs(ctx, start, other, scan, n, lsd_bytes, st, &status);
-  if (status != DPG_OK || !buckets) return status;
+  if (!buckets) {
+    int status = DPG_OK;
+    run_radix_pairs(ctx, start, other, scan, n, lsd_bytes, st, &status);
+    return status;
+  }
 
   uint4* p4 = reinterpret_cast<uint4*>(pairs);
   uint4* A = reinterpret_cast<uint4*>(tmp);
   uint4* C = reinterpret_cast<uint4*>(tmp + al(n * 16));
-  uint32_t* off = reinterpret_cast<uint32_t*>(tmp + 2 * al(n * 16));
-  uint32_t* nbig = off + kBuckets + 1;
-  uint32_t* first = nbig + 1;
-  uint32_t* counts_big = first + kBuckets;
+  {  // LSD passes on key bytes 1 and 0: pairs -> A -> pairs
+    const size_t smem = rs_tile<uint4>() * sizeof(uint4);
+    cudaFuncSetAttribute(k_rs_onesweep<uint4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int p = 0; p < 2; ++p) {
+      TraceScope ts(ctx, "k_rs_onesweep", st);
+      k_rs_onesweep<uint4><<<ntiles_of(n), kRsThreads, smem, st>>>(
+          p == 0 ? p4 : A, p == 0 ? A : p4, n, 1u - p, counts + 256 * (1 - p), state + BucketState::kStatus + p * bs.region,
+          state + BucketState::kTileCtr + p, ctx.d_err, ctx.wait_cycles);
+      ctx.launches++;
+    }
+  }
+  uint32_t* off = state + bs.off();
+  uint32_t* nbig = state + BucketState::kNbig;
+  uint32_t* first = state + bs.first();
+  uint32_t* counts_big = state + BucketState::kCountsBig;
   const int grid = ctx.sms * 8;
   {
     TraceScope ts(ctx, "k_bucket_bounds", st);
     k_bucket_bounds<<<grid, 256, 0, st>>>(p4, n, off);
     ctx.launches++;
   }
-  e = cudaMemsetAsync(nbig, 0, 4, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   {
     TraceScope ts(ctx, "k_bucket_sort", st);
     k_bucket_sort<<<grid, kBsWarps * 32, 0, st>>>(p4, off, C, nbig);
     ctx.launches++;
   }
   // the fallback for the large buckets (no pairs at all for most keys)
-  e = cudaMemsetAsync(counts_big, 0, 12 * 256 * 4, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   {
     TraceScope ts(ctx, "k_count_big", st);
     k_count_big<<<ctx.sms * 2, 256, 0, st>>>(C, nbig, key_bytes, counts_big);
@@ -652,11 +682,9 @@ int run_sort_keyptr(dpg_ctx& ctx, const uint8_t* src, uint64_t n, uint32_t rec, 
   }
   // the LSD fallback in one cooperative launch (it returns at once when no
   // bucket needed it)
-  const uint64_t region_words = (uint64_t)ntiles_of(n) * 256;
-  uint32_t* fstatus = counts_big + 12 * 256;
-  uint32_t* ctrs = fstatus + 2 * region_words;
-  e = cudaMemsetAsync(ctrs, 0, 16 * 4, st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  const uint64_t region_words = bs.region;
+  uint32_t* fstatus = state + bs.fstatus();
+  uint32_t* ctrs = state + BucketState::kCtrs;
   const size_t smem = rs_tile<uint4>() * sizeof(uint4);
   int blocks_per_sm = 0;
   e = cudaFuncSetAttribute(k_rs_passes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

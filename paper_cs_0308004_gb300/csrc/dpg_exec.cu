@@ -519,9 +519,9 @@ __device__ __forceinline__ void ex_phase_d(const ExGroup& g, const ExReq* __rest
 // the stream (V = 16 / WB), within one record or across two (W >= V); it is
 // read as V words and stored as one 16-byte vector.  Phase C: the INTERNAL
 // stream is 256-byte aligned.  Phase D: used for items that write one
-// request whose destination words of chunk q sit at a 16-byte boundary; other
-// items take the word path.  Words past the last whole chunk of an item go
-// word by word.
+// request (ex_phase_d16: the chunk grid follows the request's destination);
+// items across requests take the word path.  Words past the last whole chunk
+// of an item go word by word.
 template <int WB>
 __device__ __forceinline__ uint4 ex_pack(const typename WordT<WB>::T (&x)[16 / WB]) {
   if constexpr (WB == 4) return make_uint4(x[0], x[1], x[2], x[3]);
@@ -618,10 +618,10 @@ __device__ __forceinline__ void ex_phase_d16(const ExGroup& g, uint64_t c, uint8
   const FastDiv fdW = g.fdW;
   const uint32_t W = g.W;
   const uint64_t cw = g.cwD, i0 = c * cw, i1 = min(g.n * W, i0 + cw);
-  const uint64_t q0 = i0 / V, q1 = i1 / V;
-  // destination word of stream word t: t - begin * W (a multiple of V apart from t)
-  uint4* const dv = reinterpret_cast<uint4*>(dst) - (begin * W) / V;
-  T* const dw = reinterpret_cast<T*>(dst) - begin * W;
+  const uint64_t b0 = begin * W;  // the request's first stream word; item words t >= b0
+  const uint32_t sig = (uint32_t)(((reinterpret_cast<uintptr_t>(dst) / WB) % V + V - b0 % V) % V);
+  const uint64_t q0 = (i0 + sig + V - 1) / V, q1 = (i1 + sig) / V;  // whole chunks [q0, q1)
+  T* const dw = reinterpret_cast<T*>(dst);                        // dw[t - b0]: stream word t
   for (uint64_t qb = q0 + threadIdx.x; qb < q1; qb += (uint64_t)UC * kExThreads) {
     uint32_t sa[UC], sb[UC], w0[UC];
 #pragma unroll
@@ -629,7 +629,7 @@ __device__ __forceinline__ void ex_phase_d16(const ExGroup& g, uint64_t c, uint8
       const uint64_t q = qb + (uint64_t)u * kExThreads;
       sa[u] = sb[u] = w0[u] = 0;
       if (q < q1) {
-        const uint64_t t = q * V;
+        const uint64_t t = q * V - sig;
         const uint32_t i = (uint32_t)fdiv(t, fdW);
         w0[u] = (uint32_t)(t - (uint64_t)i * W);
         sa[u] = slot[i];
@@ -650,12 +650,18 @@ __device__ __forceinline__ void ex_phase_d16(const ExGroup& g, uint64_t c, uint8
 #pragma unroll
     for (int u = 0; u < UC; ++u) {
       const uint64_t q = qb + (uint64_t)u * kExThreads;
-      if (q < q1) dv[q] = ex_pack<WB>(x[u]);
+      if (q < q1) *reinterpret_cast<uint4*>(dw + (q * V - sig - b0)) = ex_pack<WB>(x[u]);
     }
   }
-  for (uint64_t t = q1 * V + threadIdx.x; t < i1; t += kExThreads) {
+  // words outside whole chunks: [i0, first chunk) and [after the last, i1)
+  const uint64_t h1 = q1 > q0 ? q0 * V - sig : i1, t0 = q1 > q0 ? q1 * V - sig : i1;
+  for (uint64_t t = i0 + threadIdx.x; t < h1; t += kExThreads) {
     const uint32_t i = (uint32_t)fdiv(t, fdW), w = (uint32_t)(t - (uint64_t)i * W);
-    dw[t] = iw[(uint64_t)slot[i] * W + w];
+    dw[t - b0] = iw[(uint64_t)slot[i] * W + w];
+  }
+  for (uint64_t t = t0 + threadIdx.x; t < i1; t += kExThreads) {
+    const uint32_t i = (uint32_t)fdiv(t, fdW), w = (uint32_t)(t - (uint64_t)i * W);
+    dw[t - b0] = iw[(uint64_t)slot[i] * W + w];
   }
 }
 
@@ -708,11 +714,11 @@ __device__ __forceinline__ void ex_dispatch_cd(uint32_t phase, const ExGroup& g,
   } else {
     if constexpr (V16) {
       if (chunks) {
-        // one request, its chunk words at 16-byte boundaries: the chunk path
+        // an item inside one request: the chunk path (at any WB-aligned destination)
         const uint64_t i0 = local * g.cwD, i1 = min(g.n * g.W, i0 + g.cwD);
         ex_list_reqs(g.req0, g.nreq, reqs, fdiv(i0, g.fdW), fdiv(i1 - 1, g.fdW) + 1, L);
         const uint64_t begin = L.begin[0];
-        if (L.count == 1 && (reinterpret_cast<uintptr_t>(L.dst[0]) & 15) == 0 && (begin * g.W) % (16 / WB) == 0) {
+        if (L.count == 1) {
           ex_call_d16<WB, UB>(g, local, L.dst[0], begin);
           return;
         }

@@ -608,8 +608,10 @@ __device__ __forceinline__ void ex_phase_c16(const ExGroup& g, uint64_t c, int* 
 }
 
 // Phase D of a retrieval item writing one request as 16-byte chunks (see above).
+// ex_phase_d16_range: stream words [i0, i1) of one request (begin, dst).
 template <int WB, int UB>
-__device__ __forceinline__ void ex_phase_d16(const ExGroup& g, uint64_t c, uint8_t* dst, uint64_t begin) {
+__device__ __forceinline__ void ex_phase_d16_range(const ExGroup& g, uint64_t i0, uint64_t i1, uint8_t* dst,
+                                                   uint64_t begin) {
   using T = typename WordT<WB>::T;
   constexpr uint32_t V = 16 / WB;
   constexpr int UC = UB / 16;
@@ -617,8 +619,7 @@ __device__ __forceinline__ void ex_phase_d16(const ExGroup& g, uint64_t c, uint8
   const T* __restrict__ iw = reinterpret_cast<const T*>(g.internal);
   const FastDiv fdW = g.fdW;
   const uint32_t W = g.W;
-  const uint64_t cw = g.cwD, i0 = c * cw, i1 = min(g.n * W, i0 + cw);
-  const uint64_t b0 = begin * W;  // the request's first stream word; item words t >= b0
+  const uint64_t b0 = begin * W;  // the request's first stream word; the words t >= b0
   const uint32_t sig = (uint32_t)(((reinterpret_cast<uintptr_t>(dst) / WB) % V + V - b0 % V) % V);
   const uint64_t q0 = (i0 + sig + V - 1) / V, q1 = (i1 + sig) / V;  // whole chunks [q0, q1)
   T* const dw = reinterpret_cast<T*>(dst);                        // dw[t - b0]: stream word t
@@ -663,6 +664,12 @@ __device__ __forceinline__ void ex_phase_d16(const ExGroup& g, uint64_t c, uint8
     const uint32_t i = (uint32_t)fdiv(t, fdW), w = (uint32_t)(t - (uint64_t)i * W);
     dw[t - b0] = iw[(uint64_t)slot[i] * W + w];
   }
+}
+
+template <int WB, int UB>
+__device__ __forceinline__ void ex_phase_d16(const ExGroup& g, uint64_t c, uint8_t* dst, uint64_t begin) {
+  const uint64_t i0 = c * g.cwD, i1 = min(g.n * g.W, i0 + g.cwD);
+  ex_phase_d16_range<WB, UB>(g, i0, i1, dst, begin);
 }
 
 // Calls of the phase bodies go through these non-inlined wrappers where one
@@ -837,6 +844,78 @@ __global__ void __launch_bounds__(kExThreads, MINB)
   }
 }
 
+// Phases C and D of the slot plan for groups of 4- or 8-byte words, in
+// kernels of their own: k_exec serves every word size, plan and join with
+// one register allocation (64 registers, two CTAs per SM), where these run
+// at the occupancy of the standalone gathers.  Items [item_base, n_items)
+// are claimed in order as in k_exec.  Phase C (PH = kPhaseC, retrievals and
+// joins): INTERNAL in run order as 16-byte chunks.  Phase D (retrievals): an
+// item writes its stream words request by request, as 16-byte chunks
+// aligned to each request's destination.
+constexpr int kExD16MinBlocks = 4;
+constexpr int kExD16Bytes = 32;  // bytes in flight per thread
+
+template <int WB, int PH>
+__global__ void __launch_bounds__(kExThreads, kExD16MinBlocks)
+    k_exec_cd16(const ExGroup* __restrict__ groups, const ExReq* __restrict__ reqs, const ExSeg* __restrict__ segs,
+                uint32_t nseg, uint64_t item_base, uint64_t n_items, unsigned long long* ctr, int* err) {
+  __shared__ __align__(16) ExGroup s_g;
+  __shared__ ExSeg s_sg;
+  __shared__ uint64_t s_item, s_next;
+  __shared__ uint32_t s_gidx, s_k0;
+  __shared__ int s_copy, s_go;
+  if (threadIdx.x == 0) {
+    s_gidx = 0xffffffffu;
+    s_next = error_set(err) ? n_items : item_base + atomicAdd(ctr, 1ull);
+  }
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint64_t it = s_next;
+      s_item = it;
+      if (it < n_items) {
+        // no new item once any error is set (a bad rid: nothing more is written)
+        s_next = error_set(err) ? n_items : item_base + atomicAdd(ctr, 1ull);
+        uint32_t lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (segs[mid].first <= it) lo = mid;
+          else hi = mid - 1;
+        }
+        s_sg = segs[lo];
+        s_copy = s_sg.group != s_gidx;
+        s_gidx = s_sg.group;
+        s_go = !error_set(err);
+      }
+    }
+    __syncthreads();
+    const uint64_t it = s_item;
+    if (it >= n_items) break;
+    if (s_copy)
+      for (uint32_t x = threadIdx.x; x < sizeof(ExGroup) / 8; x += kExThreads)
+        reinterpret_cast<uint64_t*>(&s_g)[x] = reinterpret_cast<const uint64_t*>(groups + s_sg.group)[x];
+    __syncthreads();
+    const ExGroup& g = s_g;
+    if constexpr (PH == (int)kPhaseC) {
+      if (s_go) ex_phase_c16<WB, kExD16Bytes>(g, it - s_sg.first, err);
+      __syncthreads();
+      continue;
+    }
+    const uint64_t i0 = (it - s_sg.first) * g.cwD, i1 = min(g.n * g.W, i0 + g.cwD);
+    if (threadIdx.x == 0) s_k0 = ex_req_of(reqs, g.req0, g.nreq, fdiv(i0, g.fdW));
+    __syncthreads();
+    if (s_go) {
+      for (uint32_t k = s_k0; k < g.req0 + g.nreq; ++k) {
+        const uint64_t b = reqs[k].begin;
+        if (b * g.W >= i1) break;
+        const uint64_t lo = max(i0, b * g.W), hi = min(i1, (b + reqs[k].n) * g.W);
+        if (lo < hi) ex_phase_d16_range<WB, kExD16Bytes>(g, lo, hi, reqs[k].dst, b);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 }  // namespace dpg
 
@@ -928,13 +1007,13 @@ void ex_plan(const dpg_ctx& c, const ExLive& q0, uint64_t n_src, uint64_t n, uin
   Retrieval r{q0.src, n_src, q0.rec, n, RidSpec{q0.rid_base, 4}, nullptr, nullptr};
   auto it = c.plans.find(plan_key(r));
   if (it != c.plans.end()) {
-    if (it->second.first == 4) {
-      *plan = kPlanSlot;
-      if (((n_src + (1ull << it->second.second) - 1) >> it->second.second) <= kExMaxRuns)
-        *sl = (uint32_t)it->second.second;
-    } else {
-      *plan = kPlanScatter;
-    }
+    // the tuner's 2-pass plan (Phase II writes each record at its
+    // destination) is the scatter plan; its L2-run and 3-pass plans (Phase II
+    // writes INTERNAL, Phase III gathers) are the slot plan, which also takes
+    // the tuned run length of an L2-run plan
+    *plan = it->second.first == 2 ? kPlanScatter : kPlanSlot;
+    if (it->second.first == 4 && ((n_src + (1ull << it->second.second) - 1) >> it->second.second) <= kExMaxRuns)
+      *sl = (uint32_t)it->second.second;
   }
   const char* e = std::getenv("DPG_EXEC_PLAN");
   if (e && !std::strcmp(e, "slot")) *plan = kPlanSlot;
@@ -1017,18 +1096,34 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
     groups.push_back(g);
     i = j;
   }
-  // items, phase by phase
+  // items, phase by phase; phase D in three runs: the retrieval groups of
+  // 4-byte words and of 8-byte words (k_exec_d16), then the rest
+  // items, phase by phase; phases C and D in three runs each: the slot-plan
+  // groups of 4-byte words and of 8-byte words (k_exec_cd16; phase D:
+  // retrievals only), then the rest
+  auto cd16_words = [](const ExGroup& g, uint32_t ph) -> uint32_t {
+    const bool ok = g.plan == kPlanSlot && (g.wb == 4 || g.wb == 8) && g.W >= 16 / g.wb && (ph == kPhaseC || !g.join);
+    return ok ? g.wb : 0u;
+  };
   std::vector<ExSeg> segs;
   uint64_t n_items = 0, n_a = 0;
-  for (uint32_t ph = kPhaseA; ph <= kPhaseD; ++ph)
-    for (uint32_t gi = 0; gi < groups.size(); ++gi) {
-      const ExGroup& g = groups[gi];
-      const uint64_t cntp = ph <= kPhaseB ? g.G : ph == kPhaseC ? g.nC : g.nD;
-      if (!cntp) continue;
-      segs.push_back(ExSeg{n_items, cntp, ph, gi});
-      n_items += cntp;
-      if (ph == kPhaseA) n_a += cntp;
+  uint64_t cd_run[2][4] = {};  // phase C / D item boundaries: 4-byte words, 8-byte words, the rest, end
+  for (uint32_t ph = kPhaseA; ph <= kPhaseD; ++ph) {
+    const bool split = ph >= kPhaseC;
+    for (int pass = 0; pass < (split ? 3 : 1); ++pass) {
+      if (split) cd_run[ph - kPhaseC][pass] = n_items;
+      for (uint32_t gi = 0; gi < groups.size(); ++gi) {
+        const ExGroup& g = groups[gi];
+        if (split && cd16_words(g, ph) != (pass == 0 ? 4u : pass == 1 ? 8u : 0u)) continue;
+        const uint64_t cntp = ph <= kPhaseB ? g.G : ph == kPhaseC ? g.nC : g.nD;
+        if (!cntp) continue;
+        segs.push_back(ExSeg{n_items, cntp, ph, gi});
+        n_items += cntp;
+        if (ph == kPhaseA) n_a += cntp;
+      }
     }
+    if (split) cd_run[ph - kPhaseC][3] = n_items;
+  }
   if (n_a > 0xffffffffULL) return DPG_EINVAL;
   // work space: the zeroed header (phase-A counter, item counter, done
   // counters, run totals), the tables, then each group's buffers
@@ -1095,7 +1190,7 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
   const size_t smem = std::max<size_t>(20 * (size_t)nb_max + kExTile * 6, (size_t)kExHistCopies * 4 * nb_max);
   uint32_t* d_done = reinterpret_cast<uint32_t*>(base + 256);
   uint32_t* d_done_a = reinterpret_cast<uint32_t*>(base);
-  unsigned long long* d_ctr = reinterpret_cast<unsigned long long*>(base + 8);  // 5 counters
+  unsigned long long* d_ctr = reinterpret_cast<unsigned long long*>(base + 8);  // 9 counters
   if (fused) {
     // one launch: every phase, dependencies by bounded waits
     auto kern = k_exec<-1, 1>;
@@ -1126,7 +1221,25 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
     // phases A and B: three CTAs per SM (40 registers); C and D: two (64)
     launch(k_exec<kPhaseA, 3>, kPhaseA, (size_t)kExHistCopies * 4 * nb_max, "k_exec_a");
     launch(k_exec<kPhaseB, 3>, kPhaseB, 20 * (size_t)nb_max + kExTile * 6, "k_exec_b");
+    // phases C and D: three runs of items each, each run with a counter of its own
+    auto launch_cd16 = [&](auto kern, uint64_t lo, uint64_t hi, unsigned long long* ctr, const char* name) {
+      if (hi <= lo) return;
+      const int per_sm = resident_per_sm(kern, kExThreads, 0);
+      const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(hi - lo, (uint64_t)c.sms * per_sm));
+      TraceScope ts(c, name, st);
+      kern<<<(uint32_t)grid, kExThreads, 0, st>>>(d_groups, d_reqs, d_segs, (uint32_t)segs.size(), lo, hi, ctr,
+                                                  c.d_err);
+      c.launches++;
+    };
+    const uint64_t(&cr)[4] = cd_run[0];
+    const uint64_t(&dr)[4] = cd_run[1];
+    launch_cd16(k_exec_cd16<4, kPhaseC>, cr[0], cr[1], d_ctr + 7, "k_exec_c16");
+    launch_cd16(k_exec_cd16<8, kPhaseC>, cr[1], cr[2], d_ctr + 8, "k_exec_c16");
+    ph_begin[kPhaseC] = cr[2];  // the rest of phase C
     launch(k_exec<kPhaseC, 2>, kPhaseC, 0, "k_exec_c");
+    launch_cd16(k_exec_cd16<4, kPhaseD>, dr[0], dr[1], d_ctr + 5, "k_exec_d16");
+    launch_cd16(k_exec_cd16<8, kPhaseD>, dr[1], dr[2], d_ctr + 6, "k_exec_d16");
+    ph_begin[kPhaseD] = dr[2];  // the rest of phase D
     launch(k_exec<kPhaseD, 2>, kPhaseD, 0, "k_exec_d");
   }
   e = cudaGetLastError();

@@ -525,7 +525,8 @@ __device__ __forceinline__ void ex_phase_d(const ExGroup& g, const ExReq* __rest
 template <int WB>
 __device__ __forceinline__ uint4 ex_pack(const typename WordT<WB>::T (&x)[16 / WB]) {
   if constexpr (WB == 4) return make_uint4(x[0], x[1], x[2], x[3]);
-  else return make_uint4(x[0].x, x[0].y, x[1].x, x[1].y);
+  else if constexpr (WB == 8) return make_uint4(x[0].x, x[0].y, x[1].x, x[1].y);
+  else return x[0];
 }
 
 template <int WB, int UB>
@@ -844,8 +845,9 @@ __global__ void __launch_bounds__(kExThreads, MINB)
   }
 }
 
-// Phases C and D of the slot plan for groups of 4- or 8-byte words, in
-// kernels of their own: k_exec serves every word size, plan and join with
+// Phases C and D of the slot plan for groups of 4-, 8- or 16-byte words
+// (WB = 4 from 3 words per record: a 16-byte chunk then spans at most two
+// records), in kernels of their own: k_exec serves every word size, plan and join with
 // one register allocation (64 registers, two CTAs per SM), where these run
 // at the occupancy of the standalone gathers.  Items [item_base, n_items)
 // are claimed in order as in k_exec.  Phase C (PH = kPhaseC, retrievals and
@@ -1098,23 +1100,23 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
   }
   // items, phase by phase; phase D in three runs: the retrieval groups of
   // 4-byte words and of 8-byte words (k_exec_d16), then the rest
-  // items, phase by phase; phases C and D in three runs each: the slot-plan
-  // groups of 4-byte words and of 8-byte words (k_exec_cd16; phase D:
-  // retrievals only), then the rest
+  // items, phase by phase; phases C and D in four runs each: the slot-plan
+  // groups k_exec_cd16 takes, by word size (phase D: retrievals only), then
+  // the rest
   auto cd16_words = [](const ExGroup& g, uint32_t ph) -> uint32_t {
-    const bool ok = g.plan == kPlanSlot && (g.wb == 4 || g.wb == 8) && g.W >= 16 / g.wb && (ph == kPhaseC || !g.join);
-    return ok ? g.wb : 0u;
+    const bool words = g.wb == 16 || g.wb == 8 || (g.wb == 4 && g.W >= 3);
+    return g.plan == kPlanSlot && words && (ph == kPhaseC || !g.join) ? g.wb : 0u;
   };
   std::vector<ExSeg> segs;
   uint64_t n_items = 0, n_a = 0;
-  uint64_t cd_run[2][4] = {};  // phase C / D item boundaries: 4-byte words, 8-byte words, the rest, end
+  uint64_t cd_run[2][5] = {};  // phase C / D item boundaries: 4-, 8-, 16-byte words, the rest, end
   for (uint32_t ph = kPhaseA; ph <= kPhaseD; ++ph) {
     const bool split = ph >= kPhaseC;
-    for (int pass = 0; pass < (split ? 3 : 1); ++pass) {
+    for (int pass = 0; pass < (split ? 4 : 1); ++pass) {
       if (split) cd_run[ph - kPhaseC][pass] = n_items;
       for (uint32_t gi = 0; gi < groups.size(); ++gi) {
         const ExGroup& g = groups[gi];
-        if (split && cd16_words(g, ph) != (pass == 0 ? 4u : pass == 1 ? 8u : 0u)) continue;
+        if (split && cd16_words(g, ph) != (pass == 0 ? 4u : pass == 1 ? 8u : pass == 2 ? 16u : 0u)) continue;
         const uint64_t cntp = ph <= kPhaseB ? g.G : ph == kPhaseC ? g.nC : g.nD;
         if (!cntp) continue;
         segs.push_back(ExSeg{n_items, cntp, ph, gi});
@@ -1122,7 +1124,7 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
         if (ph == kPhaseA) n_a += cntp;
       }
     }
-    if (split) cd_run[ph - kPhaseC][3] = n_items;
+    if (split) cd_run[ph - kPhaseC][4] = n_items;
   }
   if (n_a > 0xffffffffULL) return DPG_EINVAL;
   // work space: the zeroed header (phase-A counter, item counter, done
@@ -1190,7 +1192,7 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
   const size_t smem = std::max<size_t>(20 * (size_t)nb_max + kExTile * 6, (size_t)kExHistCopies * 4 * nb_max);
   uint32_t* d_done = reinterpret_cast<uint32_t*>(base + 256);
   uint32_t* d_done_a = reinterpret_cast<uint32_t*>(base);
-  unsigned long long* d_ctr = reinterpret_cast<unsigned long long*>(base + 8);  // 9 counters
+  unsigned long long* d_ctr = reinterpret_cast<unsigned long long*>(base + 8);  // 11 counters
   if (fused) {
     // one launch: every phase, dependencies by bounded waits
     auto kern = k_exec<-1, 1>;
@@ -1231,15 +1233,17 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
                                                   c.d_err);
       c.launches++;
     };
-    const uint64_t(&cr)[4] = cd_run[0];
-    const uint64_t(&dr)[4] = cd_run[1];
-    launch_cd16(k_exec_cd16<4, kPhaseC>, cr[0], cr[1], d_ctr + 7, "k_exec_c16");
-    launch_cd16(k_exec_cd16<8, kPhaseC>, cr[1], cr[2], d_ctr + 8, "k_exec_c16");
-    ph_begin[kPhaseC] = cr[2];  // the rest of phase C
+    const uint64_t(&cr)[5] = cd_run[0];
+    const uint64_t(&dr)[5] = cd_run[1];
+    launch_cd16(k_exec_cd16<4, kPhaseC>, cr[0], cr[1], d_ctr + 5, "k_exec_c16");
+    launch_cd16(k_exec_cd16<8, kPhaseC>, cr[1], cr[2], d_ctr + 6, "k_exec_c16");
+    launch_cd16(k_exec_cd16<16, kPhaseC>, cr[2], cr[3], d_ctr + 7, "k_exec_c16");
+    ph_begin[kPhaseC] = cr[3];  // the rest of phase C
     launch(k_exec<kPhaseC, 2>, kPhaseC, 0, "k_exec_c");
-    launch_cd16(k_exec_cd16<4, kPhaseD>, dr[0], dr[1], d_ctr + 5, "k_exec_d16");
-    launch_cd16(k_exec_cd16<8, kPhaseD>, dr[1], dr[2], d_ctr + 6, "k_exec_d16");
-    ph_begin[kPhaseD] = dr[2];  // the rest of phase D
+    launch_cd16(k_exec_cd16<4, kPhaseD>, dr[0], dr[1], d_ctr + 8, "k_exec_d16");
+    launch_cd16(k_exec_cd16<8, kPhaseD>, dr[1], dr[2], d_ctr + 9, "k_exec_d16");
+    launch_cd16(k_exec_cd16<16, kPhaseD>, dr[2], dr[3], d_ctr + 10, "k_exec_d16");
+    ph_begin[kPhaseD] = dr[3];  // the rest of phase D
     launch(k_exec<kPhaseD, 2>, kPhaseD, 0, "k_exec_d");
   }
   e = cudaGetLastError();

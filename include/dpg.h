@@ -229,9 +229,12 @@ typedef struct dpg_job {
  * DPG_JOB_JOIN, job.join_mode DPG_JOIN_MOVE: out row i = fact[i] ||
  * dim[fk_i], the layout rules of dpg_fk_join), of uneven sizes, run by a
  * persistent executor over a device table of work items (request group, DPG
- * phase, chunk) that its CTAs claim in order: one persistent launch per DPG
- * phase (four in stream order), or, with the environment variable
- * DPG_EXEC_FUSED=1, all four phases in ONE persistent launch where an item
+ * phase, chunk) that its CTAs claim in order: persistent launches in stream
+ * order, one per DPG phase for phases I (histogram and partition, two
+ * kernels) and, for phases II and III, one per word size (4, 8 or 16 bytes)
+ * of the groups that move records as 16-byte chunks plus one for the rest
+ * (at most ten per call); or, with the environment variable
+ * DPG_EXEC_FUSED=1, all phases in ONE persistent launch where an item
  * waits, with the context's wait limit (dpg_set_wait_limit), only for items
  * claimed before it.  Retrievals reading the same source table with the same record size
  * share one DPG pass over the L2-resident runs of that table (each rid is
@@ -239,7 +242,8 @@ typedef struct dpg_job {
  * group the plan is the L2-run plan through INTERNAL below 192-byte records
  * and for joins, and the fused plan that writes each record straight to its
  * destination from 192 bytes, unless dpg_tune cached a plan for the group's
- * shape.  Before anything is written every rid of every item is checked: a
+ * shape (its 2-pass plan maps to the fused plan, its L2-run and 3-pass plans
+ * to the plan through INTERNAL).  Before anything is written every rid of every item is checked: a
  * bad rid or key anywhere leaves every destination untouched and dpg_sync
  * returns DPG_ERANGE (a dimension row whose key differs from its row number
  * is found later, as in dpg_fk_join).  Work space comes from the context (one

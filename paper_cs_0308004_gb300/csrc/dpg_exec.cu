@@ -851,13 +851,15 @@ __global__ void __launch_bounds__(kExThreads, MINB)
 // one register allocation (64 registers, two CTAs per SM), where these run
 // at the occupancy of the standalone gathers.  Items [item_base, n_items)
 // are claimed in order as in k_exec.  Phase C (PH = kPhaseC, retrievals and
-// joins): INTERNAL in run order as 16-byte chunks.  Phase D (retrievals): an
+// joins): INTERNAL in run order as 16-byte chunks; SCATTER (the scatter
+// plan's retrieval groups of 16-byte words): each record straight to its
+// destination.  Phase D (retrievals): an
 // item writes its stream words request by request, as 16-byte chunks
 // aligned to each request's destination.
 constexpr int kExD16MinBlocks = 4;
 constexpr int kExD16Bytes = 32;  // bytes in flight per thread
 
-template <int WB, int PH>
+template <int WB, int PH, bool SCATTER = false>
 __global__ void __launch_bounds__(kExThreads, kExD16MinBlocks)
     k_exec_cd16(const ExGroup* __restrict__ groups, const ExReq* __restrict__ reqs, const ExSeg* __restrict__ segs,
                 uint32_t nseg, uint64_t item_base, uint64_t n_items, unsigned long long* ctr, int* err) {
@@ -899,7 +901,10 @@ __global__ void __launch_bounds__(kExThreads, kExD16MinBlocks)
     __syncthreads();
     const ExGroup& g = s_g;
     if constexpr (PH == (int)kPhaseC) {
-      if (s_go) ex_phase_c16<WB, kExD16Bytes>(g, it - s_sg.first, err);
+      if (s_go) {
+        if constexpr (SCATTER) ex_phase_c<WB, true, kExD16Bytes>(g, it - s_sg.first, err);
+        else ex_phase_c16<WB, kExD16Bytes>(g, it - s_sg.first, err);
+      }
       __syncthreads();
       continue;
     }
@@ -1100,23 +1105,26 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
   }
   // items, phase by phase; phase D in three runs: the retrieval groups of
   // 4-byte words and of 8-byte words (k_exec_d16), then the rest
-  // items, phase by phase; phases C and D in four runs each: the slot-plan
-  // groups k_exec_cd16 takes, by word size (phase D: retrievals only), then
-  // the rest
-  auto cd16_words = [](const ExGroup& g, uint32_t ph) -> uint32_t {
+  // items, phase by phase; phases C and D in runs: the groups k_exec_cd16
+  // takes, by word size and plan (phase D: retrievals only), then the rest
+  // run of a group's phase-C or phase-D items: 0, 1, 2 the lean kernel for
+  // 4-, 8-, 16-byte words; 3 (phase C) the lean scatter kernel; 4 the rest
+  auto cd_pass = [](const ExGroup& g, uint32_t ph) -> int {
+    if (ph == kPhaseC && g.plan == kPlanScatter && g.wb == 16 && !g.join) return 3;
     const bool words = g.wb == 16 || g.wb == 8 || (g.wb == 4 && g.W >= 3);
-    return g.plan == kPlanSlot && words && (ph == kPhaseC || !g.join) ? g.wb : 0u;
+    if (g.plan != kPlanSlot || !words || (ph == kPhaseD && g.join)) return 4;
+    return g.wb == 4 ? 0 : g.wb == 8 ? 1 : 2;
   };
   std::vector<ExSeg> segs;
   uint64_t n_items = 0, n_a = 0;
-  uint64_t cd_run[2][5] = {};  // phase C / D item boundaries: 4-, 8-, 16-byte words, the rest, end
+  uint64_t cd_run[2][6] = {};  // phase C / D item boundaries by run (cd_pass), then the end
   for (uint32_t ph = kPhaseA; ph <= kPhaseD; ++ph) {
     const bool split = ph >= kPhaseC;
-    for (int pass = 0; pass < (split ? 4 : 1); ++pass) {
+    for (int pass = 0; pass < (split ? 5 : 1); ++pass) {
       if (split) cd_run[ph - kPhaseC][pass] = n_items;
       for (uint32_t gi = 0; gi < groups.size(); ++gi) {
         const ExGroup& g = groups[gi];
-        if (split && cd16_words(g, ph) != (pass == 0 ? 4u : pass == 1 ? 8u : pass == 2 ? 16u : 0u)) continue;
+        if (split && cd_pass(g, ph) != pass) continue;
         const uint64_t cntp = ph <= kPhaseB ? g.G : ph == kPhaseC ? g.nC : g.nD;
         if (!cntp) continue;
         segs.push_back(ExSeg{n_items, cntp, ph, gi});
@@ -1124,7 +1132,7 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
         if (ph == kPhaseA) n_a += cntp;
       }
     }
-    if (split) cd_run[ph - kPhaseC][4] = n_items;
+    if (split) cd_run[ph - kPhaseC][5] = n_items;
   }
   if (n_a > 0xffffffffULL) return DPG_EINVAL;
   // work space: the zeroed header (phase-A counter, item counter, done
@@ -1192,7 +1200,7 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
   const size_t smem = std::max<size_t>(20 * (size_t)nb_max + kExTile * 6, (size_t)kExHistCopies * 4 * nb_max);
   uint32_t* d_done = reinterpret_cast<uint32_t*>(base + 256);
   uint32_t* d_done_a = reinterpret_cast<uint32_t*>(base);
-  unsigned long long* d_ctr = reinterpret_cast<unsigned long long*>(base + 8);  // 11 counters
+  unsigned long long* d_ctr = reinterpret_cast<unsigned long long*>(base + 8);  // 12 counters
   if (fused) {
     // one launch: every phase, dependencies by bounded waits
     auto kern = k_exec<-1, 1>;
@@ -1233,17 +1241,18 @@ int run_exec_batch(dpg_ctx& c, const dpg_batch_item* items, size_t count, cudaSt
                                                   c.d_err);
       c.launches++;
     };
-    const uint64_t(&cr)[5] = cd_run[0];
-    const uint64_t(&dr)[5] = cd_run[1];
+    const uint64_t(&cr)[6] = cd_run[0];
+    const uint64_t(&dr)[6] = cd_run[1];
     launch_cd16(k_exec_cd16<4, kPhaseC>, cr[0], cr[1], d_ctr + 5, "k_exec_c16");
     launch_cd16(k_exec_cd16<8, kPhaseC>, cr[1], cr[2], d_ctr + 6, "k_exec_c16");
     launch_cd16(k_exec_cd16<16, kPhaseC>, cr[2], cr[3], d_ctr + 7, "k_exec_c16");
-    ph_begin[kPhaseC] = cr[3];  // the rest of phase C
+    launch_cd16(k_exec_cd16<16, kPhaseC, true>, cr[3], cr[4], d_ctr + 11, "k_exec_cs16");
+    ph_begin[kPhaseC] = cr[4];  // the rest of phase C
     launch(k_exec<kPhaseC, 2>, kPhaseC, 0, "k_exec_c");
     launch_cd16(k_exec_cd16<4, kPhaseD>, dr[0], dr[1], d_ctr + 8, "k_exec_d16");
     launch_cd16(k_exec_cd16<8, kPhaseD>, dr[1], dr[2], d_ctr + 9, "k_exec_d16");
     launch_cd16(k_exec_cd16<16, kPhaseD>, dr[2], dr[3], d_ctr + 10, "k_exec_d16");
-    ph_begin[kPhaseD] = dr[3];  // the rest of phase D
+    ph_begin[kPhaseD] = dr[4];  // the rest of phase D
     launch(k_exec<kPhaseD, 2>, kPhaseD, 0, "k_exec_d");
   }
   e = cudaGetLastError();

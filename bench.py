@@ -494,7 +494,7 @@ def run_batch(a):
                       "algorithmic_bytes": alg, "steps": a.steps, "input_generation_s": round(t_gen, 1),
                       "dpg_batch_ms": round(tot_ms, 3), "dpg_batch_gbs": round(alg / tot_ms / 1e6, 1),
                       "dpg_pct_of_hbm_peak": round(alg / tot_ms / 1e6 / peak, 4),
-                      "dpg_batch_path": "persistent executor: one persistent launch per DPG phase per wave",
+                      "dpg_batch_path": "persistent executor: persistent launches per DPG phase per wave, phases II and III split by word size and plan",
                       "grouped_ms": round(tot["grouped"], 3), "grouped_gbs": round(alg / tot["grouped"] / 1e6, 1),
                       "direct_ms": round(tot_ms_direct, 3), "direct_gbs": round(alg / tot_ms_direct / 1e6, 1),
                       "speedup_vs_direct": round(tot_ms_direct / tot_ms, 4),

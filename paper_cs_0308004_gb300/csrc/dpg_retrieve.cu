@@ -831,16 +831,16 @@ Plan choose_plan(const dpg_ctx& ctx, const Retrieval& r) {
     }
   }
   // Untuned default by record size, from the 1e9-byte permutation sweep
-  // (16..128 B: L2 runs; 256 B: 2-pass shared-memory segments).  Joins: the
-  // DPG-sort join moves fact rows like a retrieval (L2 runs: 24.0 against
-  // 27.6 ms on the 2e8-row Zipf workload); DPG-move probes each dimension
-  // row about 20 times under Zipf skew: the L2-run plan's cheaper Phase I
-  // (1.1 against 5.5 ms) goes to its Phase II, whose hot rows come from the L2
-  // rather than shared memory (7.4 against 2.4 ms), so the two tie (14.8 ms)
-  // and DPG-move keeps the 3-pass plan.
+  // (16..128 B: L2 runs; 256 B: 2-pass shared-memory segments).  Joins, on
+  // the 2e8-row Zipf workload (64-byte dimension rows): the DPG-sort join
+  // moves fact rows like a retrieval (L2 runs: 24.0 against 27.6 ms); DPG-move
+  // probes each dimension row about 20 times, and the L2-run plan's cheaper
+  // Phase I (1.1 against 5.5 ms) outweighs its Phase II, whose hot rows come
+  // from the L2 rather than shared memory (4.2 against 2.4 ms): 11.6 against
+  // 14.9 ms.  Dimension rows of 192 bytes and more keep the 3-pass plan.
   // Forcing a segment size or chunk keeps the shared-memory plan.
   int dflt = r.rec < 192 ? 4 : 2;
-  if (r.join) dflt = (r.join->mode == 1 && r.rec < 192) ? 4 : 3;
+  if (r.join) dflt = r.rec < 192 ? 4 : 3;
   if (std::getenv("DPG_SEG_LOG2") || std::getenv("DPG_CHUNK")) dflt = 3;
   p.variant = env_int("DPG_VARIANT", dflt);
   const int o = env_int("DPG_SEG_LOG2", -1);

@@ -183,12 +183,13 @@ def test_join_large_every_row(ctx):
     assert torch.equal(srt, to_dev(oracle.fk_join_sorted(fact, dim)))
 
 
-@pytest.mark.parametrize("mode,variant", [("move", 3), ("sort", 4)])
-def test_join_default_plans(ctx, monkeypatch, mode, variant):
-    """Untuned joins: DPG-move on the 3-pass plan, DPG-sort on the L2-run plan."""
+@pytest.mark.parametrize("mode,dim_bytes,variant", [("move", 64, 4), ("sort", 64, 4), ("move", 256, 3)])
+def test_join_default_plans(ctx, monkeypatch, mode, dim_bytes, variant):
+    """Untuned joins: the L2-run plan, except DPG-move of dimension rows of
+    192 bytes and more (the 3-pass plan)."""
     for name in ("DPG_VARIANT", "DPG_SEG_LOG2", "DPG_CHUNK", "DPG_L2_RUN_KB", "DPG_L2_SLOT"):
         monkeypatch.delenv(name, raising=False)
-    dim, fact, fk = synth.fk_tables(4000, 90_001, 64, 16, 0.8, 13)
+    dim, fact, fk = synth.fk_tables(4000, 90_001, dim_bytes, 16, 0.8, 13)
     want = oracle.fk_join_sorted(fact, dim) if mode == "sort" else oracle.fk_join_move(fact, dim)
     out = ctx.fk_join(to_dev(fact), to_dev(dim), mode)
     ctx.sync()

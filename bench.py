@@ -96,11 +96,11 @@ def args_():
 # retrieval sources hash to `src_sha256` (any edit of them nulls the figure).
 NCU_TRAFFIC = {
     "src_sha256": "839464b6f9c43107fa9abe1d37887d452069dfd0661c7a21711c211e83abdffb"
-                  ":5bb7b838d052edacf49967a9b75593f80b9c80aff4fea6f1b12487c539627886"
+                  ":34d817e90250abc977f5ec63f21e784fbd90eb3b63ebe8ee0dea8975c34f6eba"
                   ":6a8eaedc414081fb2429ddcea50cd0f628d9e7c91ff0c6ed0a55dcd1e3c92b27",
     "n": 10_000_000, "rec": 100,
-    "bytes": {"4/k_probe_l2": 1040085504 + 960094976, "4/k_gather_phase3": 1052073728 + 954541312,
-              "3/k_probe": 1020185344 + 945171456, "3/k_gather_phase3": 1040545024 + 955424256},
+    "bytes": {"4/k_probe_l2": 1040090112 + 960025856, "4/k_gather_phase3": 1052483328 + 954384128,
+              "3/k_probe": 1020186880 + 945358080, "3/k_gather_phase3": 1040528128 + 955608320},
 }
 
 TRAFFIC_SOURCES = ("dpg_retrieve.cu", "dpg_runs.cu", "dpg_device.cuh")

@@ -330,7 +330,10 @@ __global__ void __launch_bounds__(kRunsGatherThreads, kProbeRunsMinCtas)
       const uint64_t t = base + (uint64_t)k * kRunsGatherThreads;
       if (t < total) {
         const uint32_t w = (uint32_t)(t - fdiv(t, fdW) * W);
-        v[k] = __ldcg(s + (uint64_t)id[k] * W + w);  // L2-resident run; no L1 fill (measured 400 against 407 us at 16 B)
+        // records: L2-resident run, no L1 fill (measured 400 against 407 us at
+        // 16 B); join rows (PK): hot dimension rows repeat, and an L1 copy per
+        // SM keeps their reads off the one L2 slice that holds them
+        v[k] = PK ? __ldg(s + (uint64_t)id[k] * W + w) : __ldcg(s + (uint64_t)id[k] * W + w);
         if (PK && w >= pk_w0 && w < pk_w1 && !pk_word_ok<WB>(v[k], w, pk_off, id[k])) bad = true;
       }
     }

@@ -96,11 +96,11 @@ def args_():
 # retrieval sources hash to `src_sha256` (any edit of them nulls the figure).
 NCU_TRAFFIC = {
     "src_sha256": "839464b6f9c43107fa9abe1d37887d452069dfd0661c7a21711c211e83abdffb"
-                  ":34d817e90250abc977f5ec63f21e784fbd90eb3b63ebe8ee0dea8975c34f6eba"
+                  ":7d31efd89468584f77ebb6d50328c80c41813f45939f142e68b57e2aacf98517"
                   ":6a8eaedc414081fb2429ddcea50cd0f628d9e7c91ff0c6ed0a55dcd1e3c92b27",
     "n": 10_000_000, "rec": 100,
-    "bytes": {"4/k_probe_l2": 1040090112 + 960025856, "4/k_gather_phase3": 1052483328 + 954384128,
-              "3/k_probe": 1020186880 + 945358080, "3/k_gather_phase3": 1040528128 + 955608320},
+    "bytes": {"4/k_probe_l2": 1040086784 + 960030464, "4/k_gather_phase3": 1051829504 + 954259968,
+              "3/k_probe": 1020186624 + 945471744, "3/k_gather_phase3": 1040659968 + 955471360},
 }
 
 TRAFFIC_SOURCES = ("dpg_retrieve.cu", "dpg_runs.cu", "dpg_device.cuh")

@@ -23,6 +23,11 @@ constexpr int kRunsGatherUnroll = 8;
 // the registers that takes.
 constexpr int kProbeRunsU16 = 8;
 constexpr int kProbeRunsMinCtas = 3;
+// join rows (PK): half the words in flight at twice the CTAs per SM (the
+// key check holds registers; at 64 registers the kernel ran at half the
+// SM's warp slots)
+constexpr int kProbeRunsU16Join = 4;
+constexpr int kProbeRunsMinCtasJoin = 8;
 
 // ------------------------------------------------------- L2-run plan (variant 4)
 // The paper sizes a run to half the cache (Figure 1, L = CACHE_SIZE/2).  On
@@ -292,11 +297,11 @@ __global__ void __launch_bounds__(kTileThreads, 3)
 // not raises the range bit before any output row is written.
 
 template <int WB, bool PK>
-__global__ void __launch_bounds__(kRunsGatherThreads, kProbeRunsMinCtas)
+__global__ void __launch_bounds__(kRunsGatherThreads, PK ? kProbeRunsMinCtasJoin : kProbeRunsMinCtas)
     k_probe_runs(const uint8_t* __restrict__ src, uint8_t* __restrict__ out, const uint32_t* __restrict__ run_rid,
                  uint64_t n, uint32_t W, FastDiv fdW, unsigned long long* ctr, int* err, uint32_t pk_off) {
   using T = typename WordT<WB>::T;
-  constexpr int U = WB == 16 ? kProbeRunsU16 : kRunsGatherUnroll;  // words per thread per chunk
+  constexpr int U = WB == 16 ? (PK ? kProbeRunsU16Join : kProbeRunsU16) : kRunsGatherUnroll;  // words per thread per chunk
   constexpr uint32_t CH = kRunsGatherThreads * U;
   __shared__ uint64_t s_c[2];
   if (error_set(err)) return;

@@ -143,9 +143,10 @@ dpg_status dpg_sort_records(dpg_ctx* ctx, const void* src, size_t n_src, size_t 
  *                   (ties by fact row) and fact rows moved into that order by
  *                   DPG: out[j] = fact[i_j] || dim[fk_j].
  *   DPG_JOIN_DIRECT the MOVE result in one direct pass (baseline).
- * Untuned, MOVE retrieves on the 3-pass plan and SORT on the L2-run plan (see
- * dpg_retrieve); DPG_VARIANT=4 runs MOVE on the L2-run plan too, and a forced
- * 2-pass plan falls back to the 3-pass plan (join rows need INTERNAL).
+ * Untuned, MOVE and SORT retrieve on the L2-run plan (see dpg_retrieve),
+ * except MOVE with dimension rows of 192 bytes and more, which takes the
+ * 3-pass plan; DPG_VARIANT selects a plan, and a forced 2-pass plan falls
+ * back to the 3-pass plan (join rows need INTERNAL).
  * A foreign key outside [0, n_dim), or a referenced dimension row whose key
  * differs from its row number, is reported by dpg_sync as DPG_ERANGE.  MOVE
  * and SORT catch an out-of-range key before writing `out`; MOVE also checks

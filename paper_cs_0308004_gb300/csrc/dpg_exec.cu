@@ -1,8 +1,13 @@
 // The batch executor: a whole batch of record retrievals and DPG-move joins
 // run by persistent kernels over a device table of work items (dpg_run_batch
-// and dpg_retrieve_batch in include/dpg.h): one persistent launch per DPG
-// phase, each claiming that phase's items of every group, or (fused) all
-// phases in one persistent launch.
+// and dpg_retrieve_batch in include/dpg.h): persistent launches per DPG
+// phase, each claiming that phase's items of its groups, or (fused) all
+// phases in one persistent launch.  Phases C and D are split by the groups'
+// word size and plan: the common groups (slot plan, 4-, 8- or 16-byte words;
+// for phase C also the scatter plan's 16-byte words) run in the lean
+// k_exec_cd16, one instantiation each, at four CTAs per SM; the rest runs in
+// the generic k_exec, whose one register allocation for every word size,
+// plan and join leaves it two CTAs per SM.
 //
 // Requests that read the same source table with the same record size form a
 // group (a join is a group of its own: its source is the dimension table,
